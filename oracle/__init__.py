@@ -1,0 +1,187 @@
+"""CPU FP64 oracle of the LOBPCG method (arXiv 2305.06668, Algorithms 1-3).
+
+TEST INFRASTRUCTURE ONLY.  Imported by ``tests/``, by ``__graft_entry__.smoke()`` and by
+the CPU-baseline leg of ``bench.py``; never by the GPU package.  The C source it wraps
+is plain, slow FP64 code that follows the paper's algorithms step by step.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class _Matrix(C.Structure):
+    _fields_ = [("n", C.c_int64), ("row_ptr", C.c_void_p), ("col_idx", C.c_void_p),
+                ("val", C.c_void_p), ("dense", C.c_void_p), ("ld", C.c_int64)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("k", C.c_int), ("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int),
+                ("precond", C.c_int), ("ortho_cap", C.c_int), ("ortho2_cap", C.c_int),
+                ("tol", C.c_double), ("tau", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("cholqr_passes_max", C.c_int),
+                ("ortho_passes_max", C.c_int), ("shifts", C.c_int), ("svqb", C.c_int),
+                ("cap_hits", C.c_int), ("spmm_columns", C.c_int)]
+
+
+class _Hist(C.Structure):
+    _fields_ = [("cap", C.c_int), ("lambda_", C.c_void_p), ("resnorm", C.c_void_p),
+                ("m_act", C.c_void_p), ("rows", C.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        _lib = C.CDLL(str(path))
+        _lib.oracle_lobpcg.restype = C.c_int
+        _lib.oracle_jacobi_eig.restype = C.c_int
+        _lib.oracle_cholesky.restype = C.c_int
+        _lib.oracle_ortho.restype = C.c_int
+        _lib.oracle_ortho_against.restype = C.c_int
+        _lib.oracle_threads.restype = C.c_int
+    return _lib
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def _f64(a) -> np.ndarray:
+    return np.require(a, dtype=np.float64, requirements=["F", "A", "W"]).copy(order="F")
+
+
+class Operator:
+    """Keeps the arrays alive and exposes the C struct."""
+
+    def __init__(self, csr=None, dense: np.ndarray | None = None):
+        if dense is not None:
+            self.dense = np.asfortranarray(dense, dtype=np.float64)
+            self.n = self.dense.shape[0]
+            self.s = _Matrix(self.n, None, None, None, _p(self.dense), self.n)
+        else:
+            self.row_ptr = np.ascontiguousarray(csr.row_ptr, dtype=np.int64)
+            self.col_idx = np.ascontiguousarray(csr.col_idx, dtype=np.int32)
+            self.val = np.ascontiguousarray(csr.val, dtype=np.float64)
+            self.n = csr.n
+            self.s = _Matrix(self.n, _p(self.row_ptr), _p(self.col_idx), _p(self.val), None, 0)
+
+
+def _operator(A) -> Operator:
+    if isinstance(A, Operator):
+        return A
+    if isinstance(A, np.ndarray):
+        return Operator(dense=A)
+    return Operator(csr=A)
+
+
+def apply(A, X: np.ndarray) -> np.ndarray:
+    op = _operator(A)
+    X = _f64(X.reshape(op.n, -1))
+    Y = np.zeros_like(X, order="F")
+    lib().oracle_apply(C.byref(op.s), C.c_int(X.shape[1]), _p(X), _p(Y))
+    return Y
+
+
+def jacobi_eig(a: np.ndarray):
+    a = _f64(a)
+    s = a.shape[0]
+    lam = np.zeros(s)
+    U = np.zeros((s, s), order="F")
+    sweeps = lib().oracle_jacobi_eig(C.c_int(s), _p(a), _p(lam), _p(U))
+    return lam, U, sweeps
+
+
+def cholesky(M: np.ndarray):
+    L = _f64(M)
+    fail = lib().oracle_cholesky(C.c_int(L.shape[0]), _p(L))
+    return np.tril(L), fail
+
+
+def gram(X: np.ndarray, Y: np.ndarray) -> np.ndarray:
+    X = _f64(X)
+    Y = _f64(Y)
+    Cm = np.zeros((X.shape[1], Y.shape[1]), order="F")
+    lib().oracle_gram(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X), C.c_int(Y.shape[1]), _p(Y), _p(Cm))
+    return Cm
+
+
+def svqb(X: np.ndarray) -> np.ndarray:
+    """One SVQB step (the fallback of Algorithm 2 when shifted Cholesky fails)."""
+    X = _f64(X)
+    M = gram(X, X)
+    lib().oracle_svqb(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X), _p(M))
+    return X
+
+
+def ortho(X: np.ndarray, tau: float = 1e-14, cap: int = 6):
+    """Algorithm 2.  Returns (Q, stats)."""
+    X = _f64(X)
+    sh, sv, ch, pm = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    passes = lib().oracle_ortho(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X), C.c_double(tau),
+                                C.c_int(cap), C.byref(sh), C.byref(sv), C.byref(ch), C.byref(pm))
+    return X, dict(passes=passes, shifts=sh.value, svqb=sv.value, cap_hits=ch.value)
+
+
+def ortho_against(X: np.ndarray, Y: np.ndarray, tau: float = 1e-14, cap: int = 6, cap2: int = 4):
+    """Algorithm 3.  Returns (Q, stats)."""
+    X = _f64(X)
+    Y = _f64(Y)
+    sh, sv, ch, pm = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
+    passes = lib().oracle_ortho_against(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X),
+                                        C.c_int(Y.shape[1]), _p(Y), C.c_double(tau), C.c_int(cap),
+                                        C.c_int(cap2), C.byref(sh), C.byref(sv), C.byref(ch), C.byref(pm))
+    return X, dict(passes=passes, shifts=sh.value, svqb=sv.value, cap_hits=ch.value,
+                   cholqr_passes_max=pm.value)
+
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    evals: np.ndarray
+    evecs: np.ndarray
+    resnorms: np.ndarray
+    info: dict
+    hist_lambda: np.ndarray
+    hist_res: np.ndarray
+    hist_mact: np.ndarray
+
+
+def lobpcg(A, diag, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, maxiter: int = 1000,
+           tol_kind: int = 0, precond: int = 1, tau: float = 1e-14, ortho_cap: int = 6,
+           ortho2_cap: int = 4, hist_cap: int | None = None) -> Result:
+    """Algorithm 1 on a CSR (synth.CSR) or dense (ndarray) symmetric matrix."""
+    op = _operator(A)
+    n = op.n
+    m = k + extra
+    X0 = _f64(X0)
+    assert X0.shape == (n, m), (X0.shape, n, m)
+    d = None if diag is None else np.ascontiguousarray(diag, dtype=np.float64)
+    opts = _Opts(k, extra, maxiter, tol_kind, precond, ortho_cap, ortho2_cap, tol, tau)
+    evals = np.zeros(k)
+    evecs = np.zeros((n, k), order="F")
+    res = np.zeros(k)
+    info = _Info()
+    cap = (maxiter + 1) if hist_cap is None else hist_cap
+    hl = np.zeros((cap, m))
+    hr = np.zeros((cap, m))
+    hm = np.zeros(cap, dtype=np.int32)
+    hist = _Hist(cap, _p(hl), _p(hr), _p(hm), 0)
+    st = lib().oracle_lobpcg(C.byref(op.s), _p(d), C.byref(opts), _p(X0), _p(evals), _p(evecs),
+                             _p(res), C.byref(info), C.byref(hist))
+    info_d = {f: getattr(info, f) for f, _ in _Info._fields_}
+    r = hist.rows
+    return Result(st, evals, evecs, res, info_d, hl[:r], hr[:r], hm[:r])
+
+
+def threads() -> int:
+    return lib().oracle_threads()

@@ -1,0 +1,549 @@
+/*
+ * CPU FP64 oracle for the LOBPCG eigensolver of arXiv 2305.06668.
+ *
+ * TEST INFRASTRUCTURE ONLY: loaded by the test-suite, the smoke check and the CPU
+ * baseline of the benchmark; never by the GPU library.  It is written for reading,
+ * not for speed: every step follows the paper's Algorithms 1-3 in their order and
+ * notation, with plain loops (OpenMP only spreads independent rows / matrix entries
+ * over threads, which does not change any result).
+ *
+ * Readings of points the paper leaves open (each is also listed in the design notes):
+ *  R1  Algorithm 1, initialisation: the initial Rayleigh-Ritz step solves a^[0] and
+ *      forms R = AX - X lambda from the rotated X; the lock/exit test of the main loop
+ *      is applied to this initial residual as well.
+ *  R2  The initial block is orthonormalised with Algorithm 2 first (the initial
+ *      Rayleigh-Ritz is a standard eigenproblem only for orthonormal X0).
+ *  R3  ||X^T X - I|| and ||Y^T X|| are max-abs entry norms; Algorithm 2 stops after
+ *      `ortho_cap` Cholesky-QR passes and Algorithm 3 after `ortho2_cap` projection
+ *      passes (a cap hit is counted, not an error).
+ *  R4  Shift of Sec. 3.2 / Algorithm 2: sigma_0 = 100 * eps * trace(M)
+ *      (= 100 eps ||X||_F^2, which bounds ||M||_2), multiplied by 10 after every
+ *      further failure, at most 8 shifted attempts; then an SVQB step (Stathopoulos &
+ *      Wu) with eigenvalues floored at eps * max.
+ *  R5  Algorithm 2 tests ||X^T X - I|| before each factorisation (so a successful call
+ *      costs passes + 1 Gram matrices).  Algorithm 3 runs its body at least once
+ *      (project, then ortho) and repeats while ||Y^T X|| > tau: the printed loop would
+ *      otherwise return a non-orthonormal X whenever X~ happens to be orthogonal to Y.
+ *  R6  Diagonal preconditioner (Sec. 2): w_ij = r_ij / delta with delta = d_i - lambda_j,
+ *      replaced by sign(delta) * 1e-8 * max(1, |lambda_j|) when smaller than that in
+ *      magnitude (sign(0) = +1).  Each column uses its own Ritz value.
+ *  R7  Locking (Sec. 3.1): after each Rayleigh-Ritz step the longest prefix of converged
+ *      pairs is locked; locking never undoes; locked vectors stay in X and in the
+ *      Rayleigh-Ritz problem but get no new W or P.  Exit once the first k are locked.
+ *  R8  P coefficients (Sec. 3.1, Eq. (a_block)/(neweigv)): u~_p = u_x[:, act] minus the
+ *      identity columns of the active indices in the X-block rows; then
+ *      u_p = ortho(u~_p; u_x) in R^s with Algorithm 3.
+ *  R9  The Rayleigh-Ritz matrix is symmetrised as (a + a^T) / 2 before the eigensolve.
+ *  R10 Reported residual norms are recomputed with a fresh product A X at exit.
+ */
+#include "lobpcg_oracle.h"
+
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define EPS DBL_EPSILON
+
+int oracle_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* ------------------------------------------------------------------ basic blocks */
+
+/* Pairwise (recursive halving) summation of x_i * y_i: error grows like log2(n) eps. */
+static double pairwise_dot(const double* x, const double* y, int64_t len) {
+  if (len <= 32) {
+    double s = 0.0;
+    for (int64_t i = 0; i < len; ++i) s += x[i] * y[i];
+    return s;
+  }
+  int64_t h = len / 2;
+  return pairwise_dot(x, y, h) + pairwise_dot(x + h, y + h, len - h);
+}
+
+void oracle_gram(int64_t n, int p, const double* X, int q, const double* Y, double* C) {
+  int64_t total = (int64_t)p * q;
+#pragma omp parallel for schedule(dynamic, 1)
+  for (int64_t e = 0; e < total; ++e) {
+    int i = (int)(e % p), j = (int)(e / p);
+    C[i + (int64_t)j * p] = pairwise_dot(X + (int64_t)i * n, Y + (int64_t)j * n, n);
+  }
+}
+
+/* Z = X U  (X: n x p, U: p x q, Z: n x q).  Z must not alias X. */
+static void block_times_small(int64_t n, int p, const double* X, int q, const double* U,
+                              double* Z) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < q; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < p; ++l) s += X[i + (int64_t)l * n] * U[l + (int64_t)j * p];
+      Z[i + (int64_t)j * n] = s;
+    }
+}
+
+/* X <- X - Y C  (X: n x p, Y: n x q, C: q x p). */
+static void block_minus_times(int64_t n, int p, double* X, int q, const double* Y,
+                              const double* C) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < p; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < q; ++l) s += Y[i + (int64_t)l * n] * C[l + (int64_t)j * q];
+      X[i + (int64_t)j * n] -= s;
+    }
+}
+
+void oracle_apply(const oracle_matrix* A, int p, const double* X, double* Y) {
+  const int64_t n = A->n;
+  if (A->dense) {
+    /* y_i = sum_c a_ic x_c, with a_ic = dense[i + c*ld]; column-oriented sweep. */
+    for (int j = 0; j < p; ++j) {
+      const double* x = X + (int64_t)j * n;
+      double* y = Y + (int64_t)j * n;
+#pragma omp parallel for schedule(static)
+      for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (int64_t c = 0; c < n; ++c) s += A->dense[c + i * A->ld] * x[c]; /* a_ci = a_ic */
+        y[i] = s;
+      }
+    }
+    return;
+  }
+#pragma omp parallel for schedule(dynamic, 256)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < p; ++j) {
+      double s = 0.0;
+      for (int64_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e)
+        s += A->val[e] * X[(int64_t)A->col_idx[e] + (int64_t)j * n];
+      Y[i + (int64_t)j * n] = s;
+    }
+}
+
+static double max_abs_minus_identity(int p, const double* M) {
+  double worst = 0.0;
+  for (int j = 0; j < p; ++j)
+    for (int i = 0; i < p; ++i) {
+      double v = fabs(M[i + j * p] - (i == j ? 1.0 : 0.0));
+      if (!(v <= worst)) worst = v; /* NaN propagates as "large" */
+    }
+  return worst;
+}
+
+static double max_abs(int64_t len, const double* v) {
+  double worst = 0.0;
+  for (int64_t i = 0; i < len; ++i) {
+    double a = fabs(v[i]);
+    if (!(a <= worst)) worst = a;
+  }
+  return worst;
+}
+
+/* ----------------------------------------------------------- dense small kernels */
+
+int oracle_cholesky(int p, double* M) {
+  for (int j = 0; j < p; ++j) {
+    double d = M[j + j * p];
+    for (int l = 0; l < j; ++l) d -= M[j + l * p] * M[j + l * p];
+    if (!(d > 0.0)) return j + 1;
+    double ljj = sqrt(d);
+    M[j + j * p] = ljj;
+    for (int i = j + 1; i < p; ++i) {
+      double s = M[i + j * p];
+      for (int l = 0; l < j; ++l) s -= M[i + l * p] * M[j + l * p];
+      M[i + j * p] = s / ljj;
+    }
+  }
+  return 0;
+}
+
+/* X <- X L^{-T}: each row x solves z L^T = x, i.e. L z^T = x^T (forward substitution). */
+static void right_solve_lower_transpose(int64_t n, int p, double* X, const double* L) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < p; ++j) {
+      double s = X[i + (int64_t)j * n];
+      for (int l = 0; l < j; ++l) s -= L[j + l * p] * X[i + (int64_t)l * n];
+      X[i + (int64_t)j * n] = s / L[j + j * p];
+    }
+}
+
+/* Cyclic-by-row Jacobi with the classical (smaller-angle) rotation, as in Golub & Van
+ * Loan, Matrix Computations, Sec. 8.5 (sym.schur2 + cyclic sweep). */
+int oracle_jacobi_eig(int s, const double* a_in, double* lam, double* U) {
+  double* a = (double*)malloc(sizeof(double) * (size_t)s * s);
+  double* vec = (double*)malloc(sizeof(double) * (size_t)s * s);
+  int* order = (int*)malloc(sizeof(int) * (size_t)(s > 0 ? s : 1));
+  memcpy(a, a_in, sizeof(double) * (size_t)s * s);
+  for (int j = 0; j < s; ++j)
+    for (int i = 0; i < s; ++i) vec[i + j * s] = (i == j) ? 1.0 : 0.0;
+  double fro = 0.0;
+  for (int e = 0; e < s * s; ++e) fro += a[e] * a[e];
+  fro = sqrt(fro);
+  int sweeps = 0, converged = 0;
+  for (; sweeps <= 100; ++sweeps) {
+    double off = 0.0;
+    for (int j = 0; j < s; ++j)
+      for (int i = 0; i < s; ++i)
+        if (i != j) off += a[i + j * s] * a[i + j * s];
+    if (sqrt(off) <= 1e-15 * fro) {
+      converged = 1;
+      break;
+    }
+    for (int p = 0; p < s - 1; ++p)
+      for (int q = p + 1; q < s; ++q) {
+        double apq = a[p + q * s];
+        if (apq == 0.0) continue;
+        double tau = (a[q + q * s] - a[p + p * s]) / (2.0 * apq);
+        double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        double c = 1.0 / sqrt(1.0 + t * t), sn = t * c;
+        /* A <- A J: columns p and q */
+        for (int i = 0; i < s; ++i) {
+          double aip = a[i + p * s], aiq = a[i + q * s];
+          a[i + p * s] = c * aip - sn * aiq;
+          a[i + q * s] = sn * aip + c * aiq;
+        }
+        /* A <- J^T A: rows p and q */
+        for (int j = 0; j < s; ++j) {
+          double apj = a[p + j * s], aqj = a[q + j * s];
+          a[p + j * s] = c * apj - sn * aqj;
+          a[q + j * s] = sn * apj + c * aqj;
+        }
+        a[p + q * s] = 0.0;
+        a[q + p * s] = 0.0;
+        /* U <- U J */
+        for (int i = 0; i < s; ++i) {
+          double vip = vec[i + p * s], viq = vec[i + q * s];
+          vec[i + p * s] = c * vip - sn * viq;
+          vec[i + q * s] = sn * vip + c * viq;
+        }
+      }
+  }
+  /* ascending order, ties keep index order (stable insertion sort) */
+  for (int i = 0; i < s; ++i) order[i] = i;
+  for (int i = 1; i < s; ++i) {
+    int key = order[i];
+    int j = i - 1;
+    while (j >= 0 && a[order[j] + order[j] * s] > a[key + key * s]) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = key;
+  }
+  for (int j = 0; j < s; ++j) {
+    lam[j] = a[order[j] + order[j] * s];
+    memcpy(U + (size_t)j * s, vec + (size_t)order[j] * s, sizeof(double) * (size_t)s);
+  }
+  free(a);
+  free(vec);
+  free(order);
+  return converged ? sweeps : -1;
+}
+
+/* ------------------------------------------------------ Algorithms 2 and 3 (Sec. 3.2) */
+
+/* SVQB step (Stathopoulos & Wu), the fallback when even shifted Cholesky fails:
+ * D = diag(M)^{-1/2}, D M D = Z Theta Z^T, X <- X D Z Theta^{-1/2}. */
+void oracle_svqb(int64_t n, int p, double* X, const double* M) {
+  double* dmd = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* Z = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* th = (double*)malloc(sizeof(double) * (size_t)p);
+  double* Dv = (double*)malloc(sizeof(double) * (size_t)p);
+  double* T = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* Xc = (double*)malloc(sizeof(double) * (size_t)n * p);
+  for (int i = 0; i < p; ++i) Dv[i] = M[i + i * p] > 0.0 ? 1.0 / sqrt(M[i + i * p]) : 0.0;
+  for (int j = 0; j < p; ++j)
+    for (int i = 0; i < p; ++i) dmd[i + j * p] = Dv[i] * M[i + j * p] * Dv[j];
+  oracle_jacobi_eig(p, dmd, th, Z);
+  double tmax = 0.0;
+  for (int i = 0; i < p; ++i) tmax = fmax(tmax, th[i]);
+  for (int j = 0; j < p; ++j) {
+    double t = fmax(th[j], EPS * tmax);
+    for (int i = 0; i < p; ++i) T[i + j * p] = Dv[i] * Z[i + j * p] / sqrt(t);
+  }
+  memcpy(Xc, X, sizeof(double) * (size_t)n * p);
+  block_times_small(n, p, Xc, p, T, X);
+  free(dmd), free(Z), free(th), free(Dv), free(T), free(Xc);
+}
+
+int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, int* svqb,
+                 int* cap_hit, int* passes_max) {
+  if (p <= 0) return 0;
+  double* M = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* L = (double*)malloc(sizeof(double) * (size_t)p * p);
+  int passes = 0;
+  for (;;) {
+    oracle_gram(n, p, X, p, X, M); /* M = X^T X */
+    if (max_abs_minus_identity(p, M) <= tau) break;
+    if (passes >= cap) {
+      if (cap_hit) ++*cap_hit;
+      break;
+    }
+    ++passes;
+    memcpy(L, M, sizeof(double) * (size_t)p * p);
+    int fail = oracle_cholesky(p, L);
+    if (fail) {
+      /* level shift (Sec. 3.2), grown by 10x until the factorisation succeeds */
+      double tr = 0.0;
+      for (int i = 0; i < p; ++i) tr += M[i + i * p];
+      double sigma = 100.0 * EPS * tr;
+      for (int t = 0; t < 8 && fail; ++t, sigma *= 10.0) {
+        memcpy(L, M, sizeof(double) * (size_t)p * p);
+        for (int i = 0; i < p; ++i) L[i + i * p] += sigma;
+        if (shifts) ++*shifts;
+        fail = oracle_cholesky(p, L);
+      }
+    }
+    if (fail) {
+      if (svqb) ++*svqb;
+      oracle_svqb(n, p, X, M);
+      continue;
+    }
+    right_solve_lower_transpose(n, p, X, L); /* X <- X L^{-T} */
+  }
+  if (passes_max && passes > *passes_max) *passes_max = passes;
+  free(M);
+  free(L);
+  return passes;
+}
+
+int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, double tau,
+                         int cap, int cap2, int* shifts, int* svqb, int* cap_hit,
+                         int* cholqr_passes_max) {
+  if (p <= 0) return 0;
+  double* C = (double*)malloc(sizeof(double) * (size_t)(q > 0 ? q : 1) * p);
+  int passes = 0;
+  for (;;) {
+    if (q > 0) {
+      oracle_gram(n, q, Y, p, X, C); /* C = Y^T X */
+      block_minus_times(n, p, X, q, Y, C); /* X <- X - Y Y^T X */
+    }
+    oracle_ortho(n, p, X, tau, cap, shifts, svqb, cap_hit, cholqr_passes_max);
+    ++passes;
+    if (q == 0) break;
+    oracle_gram(n, q, Y, p, X, C);
+    if (max_abs((int64_t)q * p, C) <= tau) break;
+    if (passes >= cap2) {
+      if (cap_hit) ++*cap_hit;
+      break;
+    }
+  }
+  free(C);
+  return passes;
+}
+
+/* ------------------------------------------------------------- Algorithm 1 (Sec. 3.1) */
+
+static int column_converged(int64_t n, const double* r, double tol, int tol_kind,
+                            double* norm_out) {
+  double nrm = sqrt(pairwise_dot(r, r, n));
+  *norm_out = nrm;
+  if (tol_kind == 1) {
+    double rms = nrm / sqrt((double)n);
+    return rms <= 0.1 * tol && max_abs(n, r) <= tol;
+  }
+  return nrm <= tol;
+}
+
+/* R = AX - X diag(lambda), norms and convergence flags for every column. */
+static void residuals(int64_t n, int m, const double* X, const double* AX, const double* lam,
+                      double* R, double* nrm, int* conv, double tol, int tol_kind) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j)
+      R[i + (int64_t)j * n] = AX[i + (int64_t)j * n] - lam[j] * X[i + (int64_t)j * n];
+  for (int j = 0; j < m; ++j)
+    conv[j] = column_converged(n, R + (int64_t)j * n, tol, tol_kind, &nrm[j]);
+}
+
+static void record(oracle_history* h, int m, const double* lam, const double* nrm, int m_act) {
+  if (!h || h->rows >= h->cap) return;
+  if (h->lambda) memcpy(h->lambda + (size_t)h->rows * m, lam, sizeof(double) * (size_t)m);
+  if (h->resnorm) memcpy(h->resnorm + (size_t)h->rows * m, nrm, sizeof(double) * (size_t)m);
+  if (h->m_act) h->m_act[h->rows] = m_act;
+  h->rows++;
+}
+
+/* Precondition the active residual columns (R6): W~ = T R[:, act]. */
+static void precondition(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+                         const double* diag, int precond, double* W) {
+  for (int c = 0; c < m_act; ++c) {
+    int j = m_conv + c;
+    const double* r = R + (int64_t)j * n;
+    double* w = W + (int64_t)c * n;
+    double floor_ = 1e-8 * fmax(1.0, fabs(lam[j]));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      if (precond == 1) {
+        double delta = diag[i] - lam[j];
+        if (fabs(delta) < floor_) delta = (delta >= 0.0 ? 1.0 : -1.0) * floor_;
+        w[i] = r[i] / delta;
+      } else {
+        w[i] = r[i];
+      }
+    }
+  }
+}
+
+static void finish_outputs(const oracle_matrix* A, int64_t n, int k, const double* X,
+                           const double* lam, double* evals, double* evecs, double* resnorms) {
+  double* AXk = (double*)malloc(sizeof(double) * (size_t)n * k);
+  for (int j = 0; j < k; ++j) {
+    const double* x = X + (int64_t)j * n;
+    double* e = evecs + (int64_t)j * n;
+    double big = 0.0;
+    int64_t at = 0;
+    for (int64_t i = 0; i < n; ++i)
+      if (fabs(x[i]) > big) big = fabs(x[i]), at = i;
+    double sgn = x[at] < 0.0 ? -1.0 : 1.0;
+    double nrm = sqrt(pairwise_dot(x, x, n));
+    for (int64_t i = 0; i < n; ++i) e[i] = sgn * x[i] / nrm;
+    evals[j] = lam[j];
+  }
+  oracle_apply(A, k, evecs, AXk);
+  for (int j = 0; j < k; ++j) {
+    double* r = AXk + (int64_t)j * n;
+    for (int64_t i = 0; i < n; ++i) r[i] -= evals[j] * evecs[i + (int64_t)j * n];
+    resnorms[j] = sqrt(pairwise_dot(r, r, n));
+  }
+  free(AXk);
+}
+
+int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts* opt,
+                  const double* X0, double* evals, double* evecs, double* resnorms,
+                  oracle_info* info, oracle_history* hist) {
+  const int64_t n = A->n;
+  const int k = opt->k, m = opt->k + opt->extra;
+  const double tau = opt->tau > 0 ? opt->tau : 1e-14;
+  const int cap = opt->ortho_cap > 0 ? opt->ortho_cap : 6;
+  const int cap2 = opt->ortho2_cap > 0 ? opt->ortho2_cap : 4;
+  oracle_info loc;
+  memset(&loc, 0, sizeof loc);
+  if (k < 1 || opt->extra < 0 || 3 * (int64_t)m > n || !X0 || !evals || !evecs || !resnorms)
+    return ORACLE_EINVAL;
+  if (opt->precond == 1 && !diag) return ORACLE_EINVAL;
+  if (hist) hist->rows = 0;
+
+  const int smax = 3 * m;
+  double *X = malloc(sizeof(double) * n * m), *AX = malloc(sizeof(double) * n * m);
+  double *W = malloc(sizeof(double) * n * m), *AW = malloc(sizeof(double) * n * m);
+  double *P = malloc(sizeof(double) * n * m), *AP = malloc(sizeof(double) * n * m);
+  double *R = malloc(sizeof(double) * n * m), *Y = malloc(sizeof(double) * n * 2 * m);
+  double *V = malloc(sizeof(double) * n * smax), *AV = malloc(sizeof(double) * n * smax);
+  double *a = malloc(sizeof(double) * smax * smax), *U = malloc(sizeof(double) * smax * smax);
+  double *lam_all = malloc(sizeof(double) * smax), *lam = malloc(sizeof(double) * m);
+  double *up = malloc(sizeof(double) * smax * m), *nrm = malloc(sizeof(double) * m);
+  int* conv = malloc(sizeof(int) * m);
+  if (!X || !AX || !W || !AW || !P || !AP || !R || !Y || !V || !AV || !a || !U || !lam_all ||
+      !lam || !up || !nrm || !conv) {
+    free(X), free(AX), free(W), free(AW), free(P), free(AP), free(R), free(Y), free(V);
+    free(AV), free(a), free(U), free(lam_all), free(lam), free(up), free(nrm), free(conv);
+    return ORACLE_ENOMEM;
+  }
+  int status = ORACLE_ENOCONV;
+
+  /* ---- Algorithm 1, initialisation ---- */
+  memcpy(X, X0, sizeof(double) * n * m);
+  oracle_ortho(n, m, X, tau, cap, &loc.shifts, &loc.svqb, &loc.cap_hits,
+               &loc.cholqr_passes_max);                                   /* R2 */
+  oracle_apply(A, m, X, AX);                                              /* AX = A X */
+  loc.spmm_columns += m;
+  oracle_gram(n, m, X, m, AX, a);                                         /* a = X^T AX */
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < j; ++i) a[i + j * m] = a[j + i * m] = 0.5 * (a[i + j * m] + a[j + i * m]);
+  oracle_jacobi_eig(m, a, lam, U);                                        /* a u = u lambda */
+  memcpy(V, X, sizeof(double) * n * m);
+  memcpy(AV, AX, sizeof(double) * n * m);
+  block_times_small(n, m, V, m, U, X);                                    /* X = X u, AX = AX u */
+  block_times_small(n, m, AV, m, U, AX);
+  residuals(n, m, X, AX, lam, R, nrm, conv, opt->tol, opt->tol_kind);     /* R = AX - X lambda */
+  int m_conv = 0;
+  while (m_conv < m && conv[m_conv]) ++m_conv;                            /* R1, R7 */
+  int m_act = m - m_conv;
+  record(hist, m, lam, nrm, m_act);
+  int have_p = 0, it = 0;
+  if (m_conv >= k) {
+    status = ORACLE_OK;
+    goto done;
+  }
+  precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);          /* W~ = T R */
+  {
+    int p2 = oracle_ortho_against(n, m_act, W, m, X, tau, cap, cap2, &loc.shifts, &loc.svqb,
+                                  &loc.cap_hits, &loc.cholqr_passes_max); /* W = ortho(W~; X) */
+    if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;
+  }
+  oracle_apply(A, m_act, W, AW);                                          /* AW = A W */
+  loc.spmm_columns += m_act;
+
+  /* ---- Algorithm 1, main loop ---- */
+  for (it = 1; it <= opt->maxiter; ++it) {
+    /* expansion subspace: V = (X, W) on the first pass, (X, W, P) afterwards */
+    const int s = m + m_act + (have_p ? m_act : 0);
+    memcpy(V, X, sizeof(double) * n * m);
+    memcpy(V + n * m, W, sizeof(double) * n * m_act);
+    memcpy(AV, AX, sizeof(double) * n * m);
+    memcpy(AV + n * m, AW, sizeof(double) * n * m_act);
+    if (have_p) {
+      memcpy(V + n * (m + m_act), P, sizeof(double) * n * m_act);
+      memcpy(AV + n * (m + m_act), AP, sizeof(double) * n * m_act);
+    }
+    oracle_gram(n, s, V, s, AV, a);                                       /* a = V^T AV */
+    for (int j = 0; j < s; ++j)
+      for (int i = 0; i < j; ++i)
+        a[i + j * s] = a[j + i * s] = 0.5 * (a[i + j * s] + a[j + i * s]); /* R9 */
+    oracle_jacobi_eig(s, a, lam_all, U);                                  /* Rayleigh-Ritz */
+    memcpy(lam, lam_all, sizeof(double) * m);                             /* u_x = U[:, :m] */
+    block_times_small(n, s, V, m, U, X);                                  /* X = V u_x, AX = AV u_x */
+    block_times_small(n, s, AV, m, U, AX);
+    residuals(n, m, X, AX, lam, R, nrm, conv, opt->tol, opt->tol_kind);   /* R = AX - X lambda */
+    while (m_conv < m && conv[m_conv]) ++m_conv;                          /* lock, R7 */
+    m_act = m - m_conv;
+    record(hist, m, lam, nrm, m_act);
+    if (m_conv >= k) {
+      status = ORACLE_OK;
+      break;
+    }
+    /* P coefficients: u~_p = u_x[:, act] - E_act, u_p = ortho(u~_p; u_x)  (R8) */
+    for (int c = 0; c < m_act; ++c) {
+      int j = m_conv + c;
+      memcpy(up + (size_t)c * s, U + (size_t)j * s, sizeof(double) * s);
+      up[j + (size_t)c * s] -= 1.0;
+    }
+    {
+      int p2 = oracle_ortho_against(s, m_act, up, m, U, tau, cap, cap2, &loc.shifts,
+                                    &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
+      (void)p2;
+    }
+    block_times_small(n, s, V, m_act, up, P);                             /* P = V u_p, AP = AV u_p */
+    block_times_small(n, s, AV, m_act, up, AP);
+    have_p = 1;
+    precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
+    memcpy(Y, X, sizeof(double) * n * m);                                 /* Y = (X, P) */
+    memcpy(Y + n * m, P, sizeof(double) * n * m_act);
+    {
+      int p2 = oracle_ortho_against(n, m_act, W, m + m_act, Y, tau, cap, cap2, &loc.shifts,
+                                    &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
+      if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;           /* W = ortho(W~; (X, P)) */
+    }
+    oracle_apply(A, m_act, W, AW);                                        /* AW = A W */
+    loc.spmm_columns += m_act;
+  }
+  if (it > opt->maxiter) it = opt->maxiter;
+
+done:
+  loc.iterations = it;
+  loc.converged = m_conv;
+  finish_outputs(A, n, k, X, lam, evals, evecs, resnorms);                /* R10 */
+  if (info) *info = loc;
+  free(X), free(AX), free(W), free(AW), free(P), free(AP), free(R), free(Y), free(V);
+  free(AV), free(a), free(U), free(lam_all), free(lam), free(up), free(nrm), free(conv);
+  return status;
+}

@@ -1,0 +1,108 @@
+/*
+ * CPU FP64 oracle for the LOBPCG eigensolver of "Robust and efficient LOBPCG for
+ * quantum chemistry" (arXiv 2305.06668).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the slow, plain reference that the GPU
+ * path is checked against.  Only the test-suite, the smoke check and the CPU-baseline
+ * leg of the benchmark load it; the GPU library never includes, links or calls it.
+ *
+ * Conventions: every n x p block is column-major (column j starts at X + j*n), FP64.
+ * Small p x q matrices are column-major too.
+ */
+#ifndef LOBPCG_ORACLE_H
+#define LOBPCG_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Symmetric operator: CSR (row_ptr/col_idx/val) or dense column-major (dense, ld). */
+typedef struct {
+  int64_t n;
+  const int64_t* row_ptr;
+  const int32_t* col_idx;
+  const double* val;
+  const double* dense; /* non-NULL selects the dense form */
+  int64_t ld;
+} oracle_matrix;
+
+typedef struct {
+  int k;          /* eigenpairs sought */
+  int extra;      /* block size m = k + extra (Sec. 2, larger block than sought) */
+  int maxiter;    /* iteration cap of the main loop */
+  int tol_kind;   /* 0: ||r_j||_2 <= tol;  1: rms(r_j) <= tol/10 and max|r_ij| <= tol */
+  int precond;    /* 0: none, 1: diagonal (diag(A) - theta)^-1 */
+  int ortho_cap;  /* cap on Cholesky-QR passes in ortho(X)        (default 6) */
+  int ortho2_cap; /* cap on projection passes in ortho(X, Y)      (default 4) */
+  double tol;     /* residual tolerance */
+  double tau;     /* orthogonality threshold tau_ortho (Sec. 4: 1e-14) */
+} oracle_opts;
+
+typedef struct {
+  int iterations;        /* main-loop iterations executed */
+  int converged;         /* number of leading converged (locked) pairs at exit */
+  int cholqr_passes_max; /* most Cholesky-QR passes in one ortho(X) call */
+  int ortho_passes_max;  /* most projection passes in one ortho(X, Y) call */
+  int shifts;            /* shifted Cholesky attempts, summed over the run */
+  int svqb;              /* SVQB fallbacks, summed over the run */
+  int cap_hits;          /* ortho loops that stopped at their pass cap */
+  int spmm_columns;      /* columns multiplied by A, summed over the run */
+} oracle_info;
+
+/* Per-iteration history (optional; any pointer may be NULL).  Row t (t = 0 is the
+ * initial Rayleigh-Ritz) holds the m Ritz values / residual norms and the active count. */
+typedef struct {
+  int cap;          /* rows available */
+  double* lambda;   /* cap x m, row-major */
+  double* resnorm;  /* cap x m, row-major */
+  int* m_act;       /* cap */
+  int rows;         /* rows written */
+} oracle_history;
+
+enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_ENOCONV = 4, ORACLE_EBREAKDOWN = 5 };
+
+/* Y = A X for an n x p block X. */
+void oracle_apply(const oracle_matrix* A, int p, const double* X, double* Y);
+
+/* Eigen-decomposition of a symmetric s x s matrix by cyclic Jacobi rotations.
+ * lam ascending (ties keep Jacobi's index order), U column-major s x s eigenvectors.
+ * Returns the number of sweeps, or -1 if it did not converge within 100 sweeps. */
+int oracle_jacobi_eig(int s, const double* a, double* lam, double* U);
+
+/* In-place lower Cholesky factor of p x p M (upper part untouched).
+ * Returns 0 on success, else j+1 for the first non-positive pivot j. */
+int oracle_cholesky(int p, double* M);
+
+/* C = X^T Y (p x q) with pairwise summation over the n rows. */
+void oracle_gram(int64_t n, int p, const double* X, int q, const double* Y, double* C);
+
+/* SVQB step (Stathopoulos & Wu) on X given M = X^T X: X <- X D Z Theta^{-1/2}, where
+ * D = diag(M)^{-1/2} and D M D = Z Theta Z^T (Theta floored at eps * max Theta). */
+void oracle_svqb(int64_t n, int p, double* X, const double* M);
+
+/* Algorithm 2 in place on the n x p block X.  Returns the number of Cholesky-QR
+ * passes; *shifts / *svqb / *cap_hit accumulate (may be NULL). */
+int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, int* svqb,
+                 int* cap_hit, int* passes_max);
+
+/* Algorithm 3 in place: orthonormalise X (n x p) against orthonormal Y (n x q).
+ * Returns the number of projection passes. */
+int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, double tau,
+                         int cap, int cap2, int* shifts, int* svqb, int* cap_hit,
+                         int* cholqr_passes_max);
+
+/* Algorithm 1.  diag = diag(A) (length n).  X0 = n x m initial block (m = k + extra),
+ * required.  Outputs: evals (k), evecs (n x k column-major), resnorms (k) = ||A x_j -
+ * lambda_j x_j||_2 recomputed with a fresh product.  info, hist may be NULL. */
+int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts* opt,
+                  const double* X0, double* evals, double* evecs, double* resnorms,
+                  oracle_info* info, oracle_history* hist);
+
+/* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
+int oracle_threads(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
