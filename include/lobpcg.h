@@ -1,0 +1,196 @@
+/*
+ * lobpcg.h - C ABI of the GB300 LOBPCG eigensolver.
+ *
+ * Finds the k lowest eigenpairs of a large real symmetric matrix A with the robust
+ * LOBPCG method of "Robust and efficient LOBPCG for quantum chemistry" (arXiv
+ * 2305.06668): Algorithm 1 (three-term recurrence in the orthonormal basis (X, W, P),
+ * Sec. 3.1), Algorithm 2 (shifted, repeated Cholesky-QR, Sec. 3.2), Algorithm 3
+ * (orthogonalisation against a block, Sec. 3.2), soft locking of converged pairs
+ * (Sec. 3.1, "Locking") and the diagonal preconditioner (diag(A) - theta)^-1 (Sec. 2).
+ *
+ * Every compute step runs in CUDA kernels for sm_103a.  There is no CPU fallback: a
+ * call that cannot run on the GPU returns an error status.
+ *
+ * Memory ownership
+ *   - Pointers documented as "device" must point to CUDA device memory of the current
+ *     device; "host" pointers to ordinary host memory.
+ *   - Input pointers are borrowed: the caller owns them and keeps them valid (and
+ *     unmodified) until lobpcg_destroy (matrix arrays) or until the call returns
+ *     (initial block, outputs).  The context owns every derived copy and workspace.
+ *   - Outputs are allocated by the caller.
+ *
+ * Errors
+ *   - No C++ exception or abort crosses this interface.  Every function reports a
+ *     lobpcg_status; lobpcg_last_error() returns a one-line description.
+ *   - LOBPCG_ENOCONV still fills every output with the best approximation reached.
+ *
+ * Tracing: when the environment variable LOBPCG_TRACE names a file, lobpcg_solve appends
+ * one JSON line per iteration (Ritz values, residual norms, active count).
+ *
+ * Threading: a context is used by one host thread at a time.  All work of a context
+ * is issued on the stream given to lobpcg_create; calls return after that stream has
+ * finished the work they issued.
+ */
+#ifndef LOBPCG_H
+#define LOBPCG_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LOBPCG_API __attribute__((visibility("default")))
+#else
+#define LOBPCG_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* lobpcg_stream; /* same type as cudaStream_t; NULL = legacy default stream */
+
+typedef struct lobpcg_ctx lobpcg_ctx; /* opaque; owns derived copies and workspace */
+
+typedef enum {
+  LOBPCG_OK = 0,
+  LOBPCG_EINVAL = 1,     /* invalid argument (sizes, NULL pointers, non-finite input) */
+  LOBPCG_ENOMEM = 2,     /* device or host allocation failed */
+  LOBPCG_ECUDA = 3,      /* a CUDA runtime call or kernel failed */
+  LOBPCG_ENOCONV = 4,    /* maxiter reached before the first k pairs converged */
+  LOBPCG_EBREAKDOWN = 5  /* the basis lost rank beyond what shifts / SVQB can repair */
+} lobpcg_status;
+
+typedef enum { LOBPCG_CSR = 0, LOBPCG_DENSE = 1 } lobpcg_format;
+
+typedef enum {
+  LOBPCG_PREC_NONE = 0,   /* W~ = R */
+  LOBPCG_PREC_DIAG = 1,   /* W~_ij = R_ij / (d_i - lambda_j)  (Sec. 2), guarded near zero */
+  LOBPCG_PREC_LEARNED = 2 /* diagonal preconditioner times a learned positive per-entry scale */
+} lobpcg_precond;
+
+typedef enum {
+  LOBPCG_FP64 = 0, /* every step in FP64 */
+  LOBPCG_MIXED = 1 /* FP32 storage / products until the residual stalls, then FP64 refinement */
+} lobpcg_precision;
+
+/* Symmetric input matrix.  Only the fields of the chosen format are read. */
+typedef struct {
+  lobpcg_format fmt;
+  int64_t n;              /* order of A, n >= 3 (k + extra) */
+  int64_t nnz;            /* CSR: number of stored entries (both triangles) */
+  const int64_t* row_ptr; /* CSR, device, n + 1 entries, row_ptr[0] = 0 */
+  const int32_t* col_idx; /* CSR, device, nnz column indices in [0, n) */
+  const double* val;      /* CSR, device, nnz values; A must be symmetric */
+  const double* dense;    /* DENSE, device, column-major n x n, both triangles stored */
+  int64_t ld;             /* DENSE leading dimension, ld >= n */
+  const double* diag;     /* device, length n, diag(A) (used by the preconditioner) */
+} lobpcg_matrix;
+
+typedef struct {
+  int extra;                  /* block size m = k + extra (Sec. 2); default 0 */
+  int maxiter;                /* main-loop iteration cap; default 1000 */
+  int tol_kind;               /* 0: ||r_j||_2 <= tol (default); 1: rms(r_j) <= tol/10 and max|r_ij| <= tol (Sec. 4.1) */
+  lobpcg_precond precond;     /* default LOBPCG_PREC_DIAG */
+  lobpcg_precision precision; /* default LOBPCG_FP64 */
+  double tau_ortho;           /* orthogonality threshold (Sec. 4: 1e-14); default 1e-14 */
+  int ortho_cap;              /* Cholesky-QR passes per ortho(X), default 6 */
+  int ortho2_cap;             /* projection passes per ortho(X, Y), default 4 */
+  uint64_t seed;              /* seed of the random initial block when X0 == NULL */
+  const float* mlp_weights;   /* host, learned preconditioner weights (LOBPCG_PREC_LEARNED), see lobpcg_mlp_num_weights */
+  int profile;                /* non-zero: fill lobpcg_info.phase_seconds (adds CUDA events) */
+  double mixed_switch;        /* MIXED: leave FP32 once the k sought residuals are <= this;
+                                 0 (default) = when the largest stops improving */
+} lobpcg_options;
+
+typedef struct {
+  int iterations;        /* main-loop iterations, all precision phases together */
+  int fp64_iterations;   /* of which in FP64 */
+  int converged;         /* leading pairs locked at exit */
+  int cholqr_passes_max; /* most Cholesky-QR passes in one ortho(X) */
+  int ortho_passes_max;  /* most projection passes in one ortho(X, Y) */
+  int shifts;            /* shifted Cholesky attempts */
+  int svqb;              /* SVQB fallbacks */
+  int cap_hits;          /* ortho loops stopped at their cap */
+  int64_t spmm_columns;  /* columns multiplied by A */
+  double seconds;        /* wall time of the solve on the stream (CUDA events) */
+  double phase_seconds[6]; /* with opt.profile: A products, Rayleigh-Ritz Gram, Rayleigh-Ritz
+                              eigensolve, basis update + lock, preconditioner, ortho(W; Y) */
+} lobpcg_info;
+
+/* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
+LOBPCG_API lobpcg_status lobpcg_options_default(lobpcg_options* opt);
+
+/* Creates a solver context for A (Algorithm 1 input "operator A").
+ *   out    host, receives the context (NULL on failure)
+ *   A      host struct describing device arrays (borrowed until lobpcg_destroy)
+ *   opt    host, NULL selects the defaults
+ *   stream CUDA stream every kernel of this context is issued on
+ * Errors: EINVAL for a NULL/inconsistent description, ENOMEM, ECUDA. */
+LOBPCG_API lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A, const lobpcg_options* opt,
+                            lobpcg_stream stream);
+
+/* Runs Algorithm 1 for the k lowest eigenpairs.
+ *   k         1 <= k, 3 (k + extra) <= n
+ *   tol       residual tolerance (> 0), see tol_kind
+ *   X0        device, column-major n x (k + extra) initial block, or NULL for a seeded
+ *             N(0, 1) block (Philox4x32-10 keyed by opt.seed)
+ *   evals     host, k ascending eigenvalues
+ *   evecs     device, column-major n x k eigenvectors, unit 2-norm, largest-|.|
+ *             entry positive
+ *   resnorms  host, k values ||A x_j - lambda_j x_j||_2 recomputed with a fresh product
+ *   info      host, optional (NULL)
+ * Returns OK, ENOCONV (outputs hold the best approximation), EINVAL, ENOMEM, ECUDA,
+ * EBREAKDOWN. */
+LOBPCG_API lobpcg_status lobpcg_solve(lobpcg_ctx* ctx, int k, double tol, const double* X0, double* evals,
+                           double* evecs, double* resnorms, lobpcg_info* info);
+
+/* Releases the context and everything it owns.  NULL-safe. */
+LOBPCG_API void lobpcg_destroy(lobpcg_ctx* ctx);
+
+/* Description of the last error of ctx, or (ctx == NULL) of the calling thread's last
+ * failed lobpcg_create or building-block call.  Never NULL; valid until the next call. */
+LOBPCG_API const char* lobpcg_last_error(const lobpcg_ctx* ctx);
+
+/* ------------------------------------------------------------------------------
+ * Building blocks of Algorithm 1, exposed for unit checks and for callers that drive
+ * their own iteration.  Blocks here are ROW-major: row i of an n x p block B starts at
+ * B + i*ld (ld >= p).  All arrays are device arrays; work is issued on `stream` and
+ * the call returns after the stream has finished it.
+ * ------------------------------------------------------------------------------ */
+
+/* Y = A X for CSR A (Algorithm 1, "AW = A W").  X: n x p (ldx), Y: n x p (ldy), p <= 32.
+ * Returns EINVAL for p outside [1, 32] or NULL pointers. */
+LOBPCG_API lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                  const double* val, int p, const double* X, int ldx, double* Y,
+                                  int ldy, lobpcg_stream stream);
+
+/* Y = A X for dense column-major symmetric A (lda >= n); X, Y as above, p <= 32. */
+LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64_t lda, int p,
+                                    const double* X, int ldx, double* Y, int ldy,
+                                    lobpcg_stream stream);
+
+/* C = X^T Y (the Gram / projected matrices of Algorithm 1 and Eq. (CDOrtho)).
+ * X: n x p (ldx), Y: n x q (ldy), p, q <= 96.  C: device, column-major p x q. */
+LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int ldx, int q, const double* Y,
+                              int ldy, double* C, lobpcg_stream stream);
+
+/* Symmetric eigen-decomposition of s x s column-major a (s <= 96) by parallel-order
+ * Jacobi rotations in FP64 (the Rayleigh-Ritz solve of Algorithm 1).  lam: device, s
+ * values ascending; U: device, column-major s x s eigenvectors. */
+LOBPCG_API lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U, lobpcg_stream stream);
+
+/* Algorithm 2 in place on X (n x p row-major, ldx, p <= 32).  stats (host, optional):
+ * [0] Cholesky-QR passes, [1] shifted attempts, [2] SVQB steps, [3] cap hit (0/1). */
+LOBPCG_API lobpcg_status lobpcg_ortho_f64(int64_t n, int p, double* X, int ldx, double tau, int cap,
+                               int* stats, lobpcg_stream stream);
+
+/* Algorithm 3 in place: orthonormalise X (n x p, p <= 32) against orthonormal Y
+ * (n x q, q <= 64).  stats (host, optional): [0] projection passes, [1] max
+ * Cholesky-QR passes, [2] shifted attempts, [3] SVQB steps, [4] cap hits. */
+LOBPCG_API lobpcg_status lobpcg_ortho_against_f64(int64_t n, int p, double* X, int ldx, int q,
+                                       const double* Y, int ldy, double tau, int cap, int cap2,
+                                       int* stats, lobpcg_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOBPCG_H */

@@ -28,8 +28,11 @@
  *      replaced by sign(delta) * 1e-8 * max(1, |lambda_j|) when smaller than that in
  *      magnitude (sign(0) = +1).  Each column uses its own Ritz value.
  *  R7  Locking (Sec. 3.1): after each Rayleigh-Ritz step the longest prefix of converged
- *      pairs is locked; locking never undoes; locked vectors stay in X and in the
- *      Rayleigh-Ritz problem but get no new W or P.  Exit once the first k are locked.
+ *      pairs (in the new ascending order) is locked; locked vectors stay in X and in the
+ *      Rayleigh-Ritz problem but get no new W or P.  The prefix is recomputed every
+ *      step: the Rayleigh-Ritz step can move a lower, unconverged Ritz vector in front of
+ *      a converged one, and that column must become active again.  Exit once the first
+ *      k pairs are converged.
  *  R8  P coefficients (Sec. 3.1, Eq. (a_block)/(neweigv)): u~_p = u_x[:, act] minus the
  *      identity columns of the active indices in the X-block rows; then
  *      u_p = ortho(u~_p; u_x) in R^s with Algorithm 3.
@@ -504,6 +507,7 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     block_times_small(n, s, V, m, U, X);                                  /* X = V u_x, AX = AV u_x */
     block_times_small(n, s, AV, m, U, AX);
     residuals(n, m, X, AX, lam, R, nrm, conv, opt->tol, opt->tol_kind);   /* R = AX - X lambda */
+    m_conv = 0;
     while (m_conv < m && conv[m_conv]) ++m_conv;                          /* lock, R7 */
     m_act = m - m_conv;
     record(hist, m, lam, nrm, m_act);

@@ -1,0 +1,270 @@
+"""GB300 LOBPCG eigensolver: thin Python binding of the C ABI in include/lobpcg.h.
+
+The binding only marshals arguments: every step of the method runs in the CUDA kernels
+of ``_build/liblobpcg.so``.  PyTorch supplies device memory and the current stream.
+There is no CPU fallback: without the compiled library every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import pathlib
+
+import numpy as np
+
+_HERE = pathlib.Path(__file__).resolve().parent
+_LIB_PATH = _HERE / "_build" / "liblobpcg.so"
+_lib = None
+
+OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN = range(6)
+CSR, DENSE = 0, 1
+PREC_NONE, PREC_DIAG, PREC_LEARNED = 0, 1, 2
+FP64, MIXED = 0, 1
+PHASES = ("spmm", "rr_gram", "rr_eig", "update_lock", "precond", "ortho")
+STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN"}
+
+
+class LobpcgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Matrix(C.Structure):
+    _fields_ = [("fmt", C.c_int), ("n", C.c_int64), ("nnz", C.c_int64), ("row_ptr", C.c_void_p),
+                ("col_idx", C.c_void_p), ("val", C.c_void_p), ("dense", C.c_void_p), ("ld", C.c_int64),
+                ("diag", C.c_void_p)]
+
+
+class _Options(C.Structure):
+    _fields_ = [("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int), ("precond", C.c_int),
+                ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
+                ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
+                ("mixed_switch", C.c_double)]
+
+
+class _Info(C.Structure):
+    _fields_ = [("iterations", C.c_int), ("fp64_iterations", C.c_int), ("converged", C.c_int),
+                ("cholqr_passes_max", C.c_int), ("ortho_passes_max", C.c_int), ("shifts", C.c_int),
+                ("svqb", C.c_int), ("cap_hits", C.c_int), ("spmm_columns", C.c_int64),
+                ("seconds", C.c_double), ("phase_seconds", C.c_double * 6)]
+
+
+def library_path() -> pathlib.Path:
+    return _LIB_PATH
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not _LIB_PATH.exists():
+            raise RuntimeError(f"CUDA library not built: {_LIB_PATH} is missing (run __graft_entry__.build())")
+        L = C.CDLL(str(_LIB_PATH))
+        for name in ("lobpcg_options_default", "lobpcg_create", "lobpcg_solve", "lobpcg_spmm_csr_f64",
+                     "lobpcg_spmm_dense_f64", "lobpcg_gram_f64", "lobpcg_syev_f64", "lobpcg_ortho_f64",
+                     "lobpcg_ortho_against_f64"):
+            getattr(L, name).restype = C.c_int
+        L.lobpcg_last_error.restype = C.c_char_p
+        L.lobpcg_last_error.argtypes = [C.c_void_p]
+        L.lobpcg_destroy.restype = None
+        L.lobpcg_destroy.argtypes = [C.c_void_p]
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    """Names of the C entry points declared in include/lobpcg.h."""
+    import re
+    hdr = (_HERE.parent / "include" / "lobpcg.h").read_text()
+    return re.findall(r"LOBPCG_API\s+[\w\s\*]+?\b(lobpcg_\w+)\s*\(", hdr)
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _ptr(t) -> C.c_void_p:
+    return C.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _check(status: int, ctx=None):
+    if status != OK:
+        msg = lib().lobpcg_last_error(ctx).decode()
+        raise LobpcgError(status, msg)
+
+
+def _need_cuda(t, dtype, name):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}")
+    return t
+
+
+@dataclasses.dataclass
+class Result:
+    status: int
+    evals: np.ndarray
+    evecs: object  # torch.Tensor (n, k), column-major storage
+    resnorms: np.ndarray
+    info: dict
+
+
+class Solver:
+    """Context for one symmetric matrix (lobpcg_create / lobpcg_solve / lobpcg_destroy).
+
+    CSR: pass ``row_ptr`` (int64), ``col_idx`` (int32), ``val`` (float64) CUDA tensors.
+    Dense: pass ``dense`` (float64, n x n, column-major storage or symmetric).
+    ``diag`` (float64, n) is always required.
+    """
+
+    def __init__(self, *, diag, row_ptr=None, col_idx=None, val=None, dense=None, extra: int = 0,
+                 maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
+                 tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
+                 mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, stream=None):
+        torch = _torch()
+        L = lib()
+        self._keep = [diag, row_ptr, col_idx, val, dense]
+        _need_cuda(diag, torch.float64, "diag")
+        n = diag.numel()
+        m = _Matrix()
+        if dense is not None:
+            _need_cuda(dense, torch.float64, "dense")
+            m.fmt, m.n, m.dense, m.ld = DENSE, n, dense.data_ptr(), n
+            if not (dense.is_contiguous() or dense.t().is_contiguous()):
+                raise ValueError("dense must be contiguous (row- or column-major; A is symmetric)")
+        else:
+            _need_cuda(row_ptr, torch.int64, "row_ptr")
+            _need_cuda(col_idx, torch.int32, "col_idx")
+            _need_cuda(val, torch.float64, "val")
+            m.fmt, m.n, m.nnz = CSR, n, val.numel()
+            m.row_ptr, m.col_idx, m.val = row_ptr.data_ptr(), col_idx.data_ptr(), val.data_ptr()
+        m.diag = diag.data_ptr()
+        o = _Options()
+        L.lobpcg_options_default(C.byref(o))
+        o.extra, o.maxiter, o.tol_kind, o.precond, o.precision = extra, maxiter, tol_kind, precond, precision
+        o.tau_ortho, o.ortho_cap, o.ortho2_cap, o.seed = tau_ortho, ortho_cap, ortho2_cap, seed
+        o.profile = 1 if profile else 0
+        o.mixed_switch = mixed_switch
+        w = None
+        if mlp_weights is not None:
+            w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
+            o.mlp_weights = w.ctypes.data
+        self.n, self.extra = n, extra
+        self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
+        self._ctx = C.c_void_p()
+        _check(L.lobpcg_create(C.byref(self._ctx), C.byref(m), C.byref(o), _stream(self._stream_obj)), None)
+
+    def solve(self, k: int, tol: float = 1e-8, X0=None, raise_on_noconv: bool = False) -> Result:
+        torch = _torch()
+        m = k + self.extra
+        if X0 is not None:
+            _need_cuda(X0, torch.float64, "X0")
+            if tuple(X0.shape) != (self.n, m):
+                raise ValueError(f"X0 must be {self.n} x {m}")
+            X0 = X0.t().contiguous().t()  # column-major storage
+        evecs = torch.empty((k, self.n), dtype=torch.float64, device="cuda").t()
+        evals = np.zeros(k)
+        res = np.zeros(k)
+        info = _Info()
+        st = lib().lobpcg_solve(self._ctx, C.c_int(k), C.c_double(tol), _ptr(X0),
+                                evals.ctypes.data_as(C.c_void_p), C.c_void_p(evecs.data_ptr()),
+                                res.ctypes.data_as(C.c_void_p), C.byref(info))
+        if st not in (OK, ENOCONV) or (raise_on_noconv and st == ENOCONV):
+            _check(st, self._ctx)
+        d = {f: getattr(info, f) for f, _ in _Info._fields_}
+        d["phase_seconds"] = dict(zip(PHASES, list(info.phase_seconds)))
+        return Result(st, evals, evecs, res, d)
+
+    def close(self):
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().lobpcg_destroy(self._ctx)
+            self._ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ building blocks
+# Row-major blocks: a contiguous (n, p) torch tensor is exactly the layout of the C ABI.
+
+def spmm_csr(row_ptr, col_idx, val, X, stream=None):
+    torch = _torch()
+    n, p = X.shape
+    Y = torch.empty_like(X)
+    _check(lib().lobpcg_spmm_csr_f64(C.c_int64(n), _ptr(row_ptr), _ptr(col_idx), _ptr(val), C.c_int(p),
+                                     _ptr(X), C.c_int(X.stride(0)), _ptr(Y), C.c_int(Y.stride(0)), _stream(stream)))
+    return Y
+
+
+def spmm_dense(A, X, stream=None):
+    torch = _torch()
+    n, p = X.shape
+    Y = torch.empty_like(X)
+    At = A if A.t().is_contiguous() else A.t().contiguous().t()  # column-major storage
+    _check(lib().lobpcg_spmm_dense_f64(C.c_int64(n), _ptr(At), C.c_int64(n), C.c_int(p), _ptr(X),
+                                       C.c_int(X.stride(0)), _ptr(Y), C.c_int(Y.stride(0)), _stream(stream)))
+    return Y
+
+
+def gram(X, Y, stream=None):
+    """C = X^T Y for row-major blocks X (n x p), Y (n x q)."""
+    torch = _torch()
+    n, p = X.shape
+    q = Y.shape[1]
+    Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)  # column-major p x q
+    _check(lib().lobpcg_gram_f64(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
+                                 C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
+    return Cm.t()
+
+
+def syev(a, stream=None):
+    torch = _torch()
+    s = a.shape[0]
+    ac = a.t().contiguous()  # column-major storage of a
+    lam = torch.empty(s, dtype=torch.float64, device=a.device)
+    U = torch.empty((s, s), dtype=torch.float64, device=a.device)
+    _check(lib().lobpcg_syev_f64(C.c_int(s), _ptr(ac), _ptr(lam), _ptr(U), _stream(stream)))
+    return lam, U.t()
+
+
+def ortho(X, tau=1e-14, cap=6, stream=None):
+    """Algorithm 2 in place on a row-major block; returns (X, stats)."""
+    n, p = X.shape
+    st = (C.c_int * 4)()
+    _check(lib().lobpcg_ortho_f64(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_double(tau),
+                                  C.c_int(cap), st, _stream(stream)))
+    return X, dict(passes=st[0], shifts=st[1], svqb=st[2], cap_hit=st[3])
+
+
+def ortho_against(X, Y, tau=1e-14, cap=6, cap2=4, stream=None):
+    """Algorithm 3 in place; returns (X, stats)."""
+    n, p = X.shape
+    q = 0 if Y is None else Y.shape[1]
+    st = (C.c_int * 5)()
+    _check(lib().lobpcg_ortho_against_f64(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q),
+                                          _ptr(Y), C.c_int(Y.stride(0) if q else 1), C.c_double(tau), C.c_int(cap),
+                                          C.c_int(cap2), st, _stream(stream)))
+    return X, dict(passes=st[0], cholqr_passes_max=st[1], shifts=st[2], svqb=st[3], cap_hits=st[4])
+
+
+def upload_csr(a, device="cuda"):
+    """Copy a synth.CSR-like matrix (numpy arrays) to CUDA tensors (no arithmetic)."""
+    torch = _torch()
+    return dict(row_ptr=torch.from_numpy(np.ascontiguousarray(a.row_ptr, dtype=np.int64)).to(device),
+                col_idx=torch.from_numpy(np.ascontiguousarray(a.col_idx, dtype=np.int32)).to(device),
+                val=torch.from_numpy(np.ascontiguousarray(a.val, dtype=np.float64)).to(device),
+                diag=torch.from_numpy(np.ascontiguousarray(a.diag, dtype=np.float64)).to(device))

@@ -1,0 +1,172 @@
+// Shared device helpers and the internal launch interface of the GB300 LOBPCG library.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+
+namespace lobpcg {
+
+constexpr int kMaxS = 96;     // largest Rayleigh-Ritz size s = m + 2 m_act (m <= 32)
+constexpr int kMaxM = 32;     // largest block width m = k + extra
+constexpr int kWarp = 32;
+
+struct CudaError : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+#define LB_CUDA(call)                                                                      \
+  do {                                                                                     \
+    cudaError_t e_ = (call);                                                               \
+    if (e_ != cudaSuccess)                                                                 \
+      throw ::lobpcg::CudaError(std::string(#call) + ": " + cudaGetErrorString(e_) + " (" + \
+                                __FILE__ + ":" + std::to_string(__LINE__) + ")");          \
+  } while (0)
+
+#define LB_LAUNCH_CHECK() LB_CUDA(cudaGetLastError())
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ inline int64_t ceil_div_dev(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// A logical n x w block made of up to three row-major segments placed side by side
+// (the expansion basis V = [X | P | W] and AV = [AX | AP | AW]).
+template <class T>
+struct Cols {
+  const T* p[3];
+  int ld[3];
+  int w[3];
+  int nseg;
+  __host__ __device__ int width() const {
+    int s = 0;
+    for (int i = 0; i < nseg; ++i) s += w[i];
+    return s;
+  }
+};
+
+template <class T>
+inline Cols<T> cols1(const T* p, int ld, int w) {
+  Cols<T> c{};
+  c.p[0] = p, c.ld[0] = ld, c.w[0] = w, c.nseg = w > 0 ? 1 : 0;
+  return c;
+}
+template <class T>
+inline Cols<T> cols_add(Cols<T> c, const T* p, int ld, int w) {
+  if (w > 0) {
+    c.p[c.nseg] = p, c.ld[c.nseg] = ld, c.w[c.nseg] = w;
+    c.nseg++;
+  }
+  return c;
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ----------------------------------------------------------------------------------
+// Launch wrappers (host side).  All take the stream; none synchronises.
+// ----------------------------------------------------------------------------------
+
+// Y = A X, CSR, row-major blocks.  p <= 32.
+template <class T, class V>
+void launch_spmm_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val,
+                     int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st);
+// Y = A X, dense column-major symmetric A.
+template <class T>
+void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, int ldx, T* Y,
+                       int ldy, cudaStream_t st);
+
+// Gram partials: part[g][i + j*pa] = sum over CTA g's rows of a_ri * b_rj.
+// upper: only i <= j entries are produced.  Returns the number of CTAs used.
+template <class T>
+int gram_partials(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, double* part,
+                  int max_ctas, cudaStream_t st);
+// out[e] = sum_g part[g][e] for e < count (FP64, fixed order).
+void reduce_partials(const double* part, int nparts, int count, double* out, cudaStream_t st);
+
+// out_t = base_t + alpha * in_t * U for t = 0..nprod-1 (U: s x q column-major FP64 on device).
+// in_t: Cols of width s; out_t/base_t row-major (ld).  base_t may be null (then 0).
+// When norm_part != null (nprod == 2, out0 = X, out1 = AX): also accumulates per-column
+// partial sums of r_ij^2 and max |r_ij| with r = AX - X diag(lam) into norm_part[cta][2*q].
+template <class T>
+struct UpdateJob {
+  Cols<T> in[2];
+  T* out[2];
+  int ld_out[2];
+  const T* base[2];
+  int ld_base[2];
+  int nprod;
+};
+template <class T>
+int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
+                  const double* lam, double* norm_part, int max_ctas, cudaStream_t st);
+
+// W~_ij = R_ij / guard(d_i - lam_{c0+j}) (precond 1) or R_ij (precond 0) with
+// R = AX[:, c0+j] - lam_{c0+j} X[:, c0+j], j < a.
+template <class T>
+void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
+                    const double* diag, int precond, T* W, int ldw, cudaStream_t st);
+
+// row-major (ld) <-> column-major (n x p) conversions, optional precision change.
+template <class Tin, class Tout>
+void launch_colmajor_to_rows(int64_t n, int p, const Tin* src, Tout* dst, int ld, cudaStream_t st);
+template <class Tin, class Tout>
+void launch_rows_to_colmajor(int64_t n, int p, const Tin* src, int ld, Tout* dst, cudaStream_t st);
+// Seeded N(0,1) column-major block (Philox4x32-10 + Box-Muller).
+void launch_gaussian(int64_t n, int p, uint64_t seed, double* dst, cudaStream_t st);
+// dst[i] = (float) src[i]
+void launch_to_float(int64_t count, const double* src, float* dst, cudaStream_t st);
+// true if every entry is finite (result written to *flag on device as 0/1)
+void launch_all_finite(int64_t count, const double* src, int* flag, cudaStream_t st);
+
+// ---- small FP64 kernels (one CTA) ----
+// Symmetric eigensolve: a (s x s, column-major; only the upper triangle is read when
+// upper_only) -> lam ascending, U column-major.  sweeps_out: device int (may be null).
+void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U, int* sweeps_out,
+                 cudaStream_t st);
+
+// Cholesky-QR step on the reduced Gram matrix M (p x p, column-major):
+//  ctl[0] <- 1 if max|M - I| <= tau (already orthonormal), else 0 and Linv <- L^{-T}
+//  of chol(M + shift) (upper triangular, column-major p x p).  ctl[1] += shifted
+//  attempts, ctl[2] += 1 if SVQB had to be used (then Linv holds the SVQB transform).
+void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl,
+                         cudaStream_t st);
+// max |C| over a p x q matrix -> *out (device double)
+void launch_maxabs(int count, const double* C, double* out, cudaStream_t st);
+
+// Lock decision + P coefficients (Algorithm 1, lock and u_p steps):
+//  reads norm partials (nparts x 2m), lam (m), U (s x s), state -> writes resnorm (m),
+//  new m_conv / m_act, done flag, and u_p (s x m_act) = ortho(u_x[:,act] - E_act; u_x).
+struct LockState {
+  int m_conv;
+  int m_act;
+  int done;
+  int sp_shifts;
+  int sp_passes;
+};
+void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, int nparts,
+                       const double* U, double tol, int tol_kind, double tau, LockState* state,
+                       double* resnorm, double* up, bool build_p, cudaStream_t st);
+
+}  // namespace lobpcg
+
+namespace lobpcg {
+// Per-column largest |x_ij| with its sign (ties: smallest row) for the first p columns
+// of a row-major block; writes sign (+1/-1) per column into sgn (device double).
+template <class T>
+void launch_col_sign(int64_t n, int p, const T* X, int ld, double* part, int max_ctas, double* sgn,
+                     cudaStream_t st);
+// scale[j] = sgn[j] / sqrt(G[j + j*p]) written as a p x p diagonal matrix S (column-major).
+void launch_scale_matrix(int p, const double* G, const double* sgn, double* S, cudaStream_t st);
+}  // namespace lobpcg

@@ -1,0 +1,489 @@
+// Small FP64 kernels, one CTA each: the Rayleigh-Ritz eigensolve (parallel-order
+// Jacobi), the Cholesky-QR step with level shift / SVQB fallback (Algorithm 2, Sec. 3.2),
+// the lock decision and the P coefficients u_p = ortho(u~_p; u_x) (Algorithm 1, Sec.
+// 3.1), all in shared memory.
+#include <cfloat>
+
+#include "common.cuh"
+
+namespace lobpcg {
+namespace {
+
+constexpr int kSmallThreads = 512;
+constexpr int kMaxCholP = 64;  // largest block orthonormalised by the Cholesky-QR kernel
+
+// Block-wide reductions (all threads must call; result returned to every thread).
+__device__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  __syncthreads();
+  return s;
+}
+__device__ double block_max(double v, double* red) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s = fmax(s, red[i]);
+  __syncthreads();
+  return s;
+}
+
+// Parallel-order (round-robin) cyclic Jacobi on the symmetric s x s matrix a (column-
+// major, leading dimension lda, overwritten by its rotated form) accumulating the
+// rotations in V (s x s, ldv).  Each round applies s/2 disjoint rotations (classical
+// smaller-angle rotation of Golub & Van Loan, Sec. 8.5) as J^T A then A J.
+// Returns the number of sweeps, or -1 without convergence in 40 sweeps.
+__device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double* rot, double* red) {
+  const int N = s + (s & 1);
+  const int half = N / 2;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    V[i + j * ldv] = i == j ? 1.0 : 0.0;
+  }
+  double f2 = 0.0;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const double v = a[(e % s) + (e / s) * lda];
+    f2 += v * v;
+  }
+  const double fro = sqrt(block_sum(f2, red));
+  int sweep = 0;
+  for (; sweep < 40; ++sweep) {
+    double o2 = 0.0;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      if (i != j) {
+        const double v = a[i + j * lda];
+        o2 += v * v;
+      }
+    }
+    const double off = sqrt(block_sum(o2, red));
+    if (off <= 1e-15 * fro || off == 0.0) return sweep;
+    for (int r = 0; r < N - 1; ++r) {
+      // phase A: rotation of every pair of this round (circle method, player N-1 fixed)
+      for (int i = threadIdx.x; i < half; i += blockDim.x) {
+        int p, q;
+        if (i == 0) p = N - 1, q = r;
+        else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        bool skip = q >= s;
+        if (!skip) {
+          const double apq = a[p + q * lda];
+          if (apq == 0.0) {
+            skip = true;
+          } else {
+            const double tau = (a[q + q * lda] - a[p + p * lda]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+          }
+        }
+        rot[4 * i + 0] = skip ? -1.0 : (double)p;
+        rot[4 * i + 1] = (double)q;
+        rot[4 * i + 2] = c;
+        rot[4 * i + 3] = sn;
+      }
+      __syncthreads();
+      // phase B: rows p, q of a (J^T A) and columns p, q of V (V J)
+      for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        if (rot[4 * i] < 0.0) continue;
+        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const double c = rot[4 * i + 2], sn = rot[4 * i + 3];
+        const double apj = a[p + j * lda], aqj = a[q + j * lda];
+        a[p + j * lda] = c * apj - sn * aqj;
+        a[q + j * lda] = sn * apj + c * aqj;
+        const double vjp = V[j + p * ldv], vjq = V[j + q * ldv];
+        V[j + p * ldv] = c * vjp - sn * vjq;
+        V[j + q * ldv] = sn * vjp + c * vjq;
+      }
+      __syncthreads();
+      // phase C: columns p, q of a (A J); the annihilated pair is set to exactly zero
+      for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        if (rot[4 * i] < 0.0) continue;
+        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const double c = rot[4 * i + 2], sn = rot[4 * i + 3];
+        const double ajp = a[j + p * lda], ajq = a[j + q * lda];
+        double np = c * ajp - sn * ajq, nq = sn * ajp + c * ajq;
+        if (j == p) nq = 0.0;
+        if (j == q) np = 0.0;
+        a[j + p * lda] = np;
+        a[j + q * lda] = nq;
+      }
+      __syncthreads();
+    }
+  }
+  return -1;
+}
+
+// Write eigenvalues (diagonal of the rotated a) ascending with their V columns;
+// ties keep index order.
+__device__ void sort_eig(int s, const double* a, int lda, const double* V, int ldv, double* lam,
+                         double* U) {
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    const double li = a[i + i * lda];
+    int rank = 0;
+    for (int j = 0; j < s; ++j) {
+      const double lj = a[j + j * lda];
+      rank += (lj < li) || (lj == li && j < i);
+    }
+    lam[rank] = li;
+    for (int r = 0; r < s; ++r) U[r + rank * s] = V[r + i * ldv];
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double* __restrict__ a_in,
+                                                             int upper_only, double* __restrict__ lam,
+                                                             double* __restrict__ U, int* sweeps_out) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double rot[4 * (kMaxS / 2 + 1)];
+  const int lda = s + 1;  // odd stride against bank conflicts
+  double* a = sm;
+  double* V = sm + s * lda;
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int i = e % s, j = e / s;
+    double v;
+    if (upper_only) v = i <= j ? a_in[i + j * s] : a_in[j + i * s];
+    else v = 0.5 * (a_in[i + j * s] + a_in[j + i * s]);
+    a[i + j * lda] = v;
+  }
+  __syncthreads();
+  const int sw = jacobi_cta(s, a, lda, V, lda, rot, red);
+  __syncthreads();
+  sort_eig(s, a, lda, V, lda, lam, U);
+  if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+}
+
+// In-place right-looking Cholesky of the p x p matrix L (lower part, ld).  Returns 0 or
+// j+1 for the first non-positive pivot (same value in every thread).
+__device__ int chol_cta(int p, double* L, int ld, int* flag) {
+  if (threadIdx.x == 0) *flag = 0;
+  __syncthreads();
+  for (int j = 0; j < p; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = L[j + j * ld];
+      if (!(d > 0.0)) *flag = j + 1;
+      else L[j + j * ld] = sqrt(d);
+    }
+    __syncthreads();
+    if (*flag) break;
+    const double ljj = L[j + j * ld];
+    for (int i = j + 1 + threadIdx.x; i < p; i += blockDim.x) L[i + j * ld] /= ljj;
+    __syncthreads();
+    const int rem = p - j - 1;
+    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
+      const int i = j + 1 + e % rem, l = j + 1 + e / rem;
+      if (l <= i) L[i + l * ld] -= L[i + j * ld] * L[l + j * ld];
+    }
+    __syncthreads();
+  }
+  const int f = *flag;
+  __syncthreads();
+  return f;
+}
+
+// Shifted Cholesky of M (p x p, ld): tries M, then M + sigma I with sigma = 100 eps
+// trace(M) * 10^t, t = 0..7.  L receives the factor.  Returns 0 on success.
+__device__ int shifted_chol_cta(int p, const double* M, int ldm, double* L, int ld, int* flag,
+                                int* shifts, double* red) {
+  double tr = 0.0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) tr += M[i + i * ldm];
+  tr = block_sum(tr, red);
+  int fail = 1;
+  for (int t = -1; t < 8 && fail; ++t) {
+    const double sigma = t < 0 ? 0.0 : 100.0 * DBL_EPSILON * tr * pow(10.0, (double)t);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      const int i = e % p, j = e / p;
+      L[i + j * ld] = M[i + j * ldm] + (i == j ? sigma : 0.0);
+    }
+    __syncthreads();
+    if (t >= 0 && threadIdx.x == 0) ++*shifts;
+    fail = chol_cta(p, L, ld, flag);
+  }
+  return fail;
+}
+
+// T = L^{-T} (upper triangular p x p, column-major, ldt) from the lower factor L.
+__device__ void inv_lower_transpose_cta(int p, const double* L, int ld, double* T, int ldt) {
+  // column j of L^{-1} by forward substitution; written transposed into row j of T
+  for (int j = threadIdx.x; j < p; j += blockDim.x) {
+    for (int i = 0; i < p; ++i) T[j + i * ldt] = 0.0;
+    for (int i = j; i < p; ++i) {
+      double s = i == j ? 1.0 : 0.0;
+      for (int l = j; l < i; ++l) s -= L[i + l * ld] * T[j + l * ldt];
+      T[j + i * ldt] = s / L[i + i * ld];
+    }
+  }
+  __syncthreads();
+}
+
+// SVQB transform T = D Z Theta^{-1/2} for Gram M (Stathopoulos & Wu).  Uses B (p x p,
+// ldb) and Z as scratch.
+__device__ void svqb_cta(int p, const double* M, int ldm, double* B, double* Z, int ldb, double* T,
+                         int ldt, double* rot, double* red, double* theta) {
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e % p, j = e / p;
+    const double di = M[i + i * ldm] > 0.0 ? rsqrt(M[i + i * ldm]) : 0.0;
+    const double dj = M[j + j * ldm] > 0.0 ? rsqrt(M[j + j * ldm]) : 0.0;
+    B[i + j * ldb] = di * M[i + j * ldm] * dj;
+  }
+  __syncthreads();
+  jacobi_cta(p, B, ldb, Z, ldb, rot, red);
+  __syncthreads();
+  double tmax = 0.0;
+  for (int i = threadIdx.x; i < p; i += blockDim.x) tmax = fmax(tmax, B[i + i * ldb]);
+  tmax = block_max(tmax, red);
+  for (int i = threadIdx.x; i < p; i += blockDim.x) theta[i] = fmax(B[i + i * ldb], DBL_EPSILON * tmax);
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e % p, j = e / p;
+    const double di = M[i + i * ldm] > 0.0 ? rsqrt(M[i + i * ldm]) : 0.0;
+    T[i + j * ldt] = di * Z[i + j * ldb] / sqrt(theta[j]);
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSmallThreads) cholqr_small_kernel(int p, const double* __restrict__ Min,
+                                                                     double tau, double* __restrict__ Tout,
+                                                                     int* ctl) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double rot[4 * (kMaxS / 2 + 1)];
+  __shared__ double theta[kMaxS];
+  __shared__ int flag, shifts;
+  const int ld = p + 1;
+  double* M = sm;
+  double* L = M + p * ld;
+  double* T = L + p * ld;
+  double* Z = T + p * ld;
+  double dev = 0.0;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e % p, j = e / p;
+    const double v = Min[e];
+    M[i + j * ld] = v;
+    const double d = fabs(v - (i == j ? 1.0 : 0.0));
+    dev = (d <= dev) ? dev : d;  // NaN counts as large
+    if (d != d) dev = INFINITY;
+  }
+  if (threadIdx.x == 0) shifts = 0;
+  dev = block_max(dev, red);
+  if (dev <= tau) {
+    if (threadIdx.x == 0) ctl[0] = 1;
+    return;
+  }
+  const int fail = shifted_chol_cta(p, M, ld, L, ld, &flag, &shifts, red);
+  if (!fail) {
+    inv_lower_transpose_cta(p, L, ld, T, ld);
+  } else {
+    svqb_cta(p, M, ld, L, Z, ld, T, ld, rot, red, theta);
+  }
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) Tout[e] = T[(e % p) + (e / p) * ld];
+  if (threadIdx.x == 0) {
+    ctl[0] = 0;
+    ctl[1] += shifts;
+    ctl[2] += fail ? 1 : 0;
+  }
+}
+
+__global__ void maxabs_kernel(int count, const double* __restrict__ C, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int e = threadIdx.x; e < count; e += blockDim.x) {
+    const double v = fabs(C[e]);
+    m = (v <= m) ? m : v;
+    if (v != v) m = INFINITY;
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) *out = m;
+}
+
+// ---- Algorithm 2 / 3 in the small s-dimensional space (for u_p) -----------------------
+// X: s x a (column-major, ldx), Y: s x q (ldy); everything in shared memory.
+__device__ void small_ortho(int s, int a, double* X, int ldx, double tau, int cap, double* M,
+                            double* L, double* Tm, double* Z, int ld, double* rot, double* red,
+                            double* theta, int* flag, int* shifts) {
+  for (int pass = 0;; ++pass) {
+    for (int e = threadIdx.x; e < a * a; e += blockDim.x) {
+      const int i = e % a, j = e / a;
+      double acc = 0.0;
+      for (int r = 0; r < s; ++r) acc += X[r + i * ldx] * X[r + j * ldx];
+      M[i + j * ld] = acc;
+    }
+    __syncthreads();
+    double dev = 0.0;
+    for (int e = threadIdx.x; e < a * a; e += blockDim.x) {
+      const double d = fabs(M[(e % a) + (e / a) * ld] - ((e % a) == (e / a) ? 1.0 : 0.0));
+      dev = (d <= dev) ? dev : d;
+      if (d != d) dev = INFINITY;
+    }
+    dev = block_max(dev, red);
+    if (dev <= tau || pass >= cap) return;
+    const int fail = shifted_chol_cta(a, M, ld, L, ld, flag, shifts, red);
+    if (!fail) inv_lower_transpose_cta(a, L, ld, Tm, ld);
+    else svqb_cta(a, M, ld, L, Z, ld, Tm, ld, rot, red, theta);
+    // X <- X Tm, row by row (each thread owns rows of X)
+    for (int r = threadIdx.x; r < s; r += blockDim.x) {
+      double row[kMaxM];
+      for (int j = 0; j < a; ++j) row[j] = X[r + j * ldx];
+      for (int j = 0; j < a; ++j) {
+        double acc = 0.0;
+        for (int l = 0; l < a; ++l) acc += row[l] * Tm[l + j * ld];
+        X[r + j * ldx] = acc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int k, int64_t n,
+                                                               const double* __restrict__ norm_part,
+                                                               int nparts, const double* __restrict__ U,
+                                                               double tol, int tol_kind, double tau,
+                                                               LockState* state, double* __restrict__ resnorm,
+                                                               double* __restrict__ up, int build_p) {
+  extern __shared__ double sm[];
+  __shared__ double red[32];
+  __shared__ double rot[4 * (kMaxS / 2 + 1)];
+  __shared__ double theta[kMaxS];
+  __shared__ int conv[kMaxM];
+  __shared__ int flag, shifts, s_mconv, s_mact, s_done;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double s2 = 0.0, mx = 0.0;
+    for (int g = 0; g < nparts; ++g) {
+      s2 += norm_part[(int64_t)g * 2 * m + j];
+      mx = fmax(mx, norm_part[(int64_t)g * 2 * m + m + j]);
+    }
+    const double nr = sqrt(s2);
+    resnorm[j] = nr;
+    conv[j] = tol_kind == 1 ? (nr / sqrt((double)n) <= 0.1 * tol && mx <= tol) : (nr <= tol);
+  }
+  if (threadIdx.x == 0) shifts = 0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // longest converged prefix in the new Ritz order (recomputed every step: a lower,
+    // unconverged Ritz vector can move in front of a converged one)
+    int mc = 0;
+    while (mc < m && conv[mc]) ++mc;
+    s_mconv = mc;
+    s_mact = m - mc;
+    s_done = mc >= k;
+    state->m_conv = mc;
+    state->m_act = m - mc;
+    state->done = s_done;
+  }
+  __syncthreads();
+  if (!build_p || s_done) return;
+  const int mc = s_mconv, a = s_mact;
+  const int ld = kMaxS + 1;        // s-dimensional columns
+  const int lds = kMaxM + 1;       // a x a / m x a matrices
+  double* X = sm;                  // s x a   (ld)
+  double* Y = X + kMaxM * ld;      // s x m   (ld), u_x
+  double* C = Y + kMaxM * ld;      // m x a   (lds)
+  double* M = C + kMaxM * lds;     // a x a   (lds) and scratch
+  double* L = M + kMaxM * lds;
+  double* Tm = L + kMaxM * lds;
+  double* Z = Tm + kMaxM * lds;
+  for (int e = threadIdx.x; e < s * a; e += blockDim.x) {
+    const int r = e % s, c = e / s;
+    X[r + c * ld] = U[r + (mc + c) * s] - (r == mc + c ? 1.0 : 0.0);  // u~_p = u_x[:,act] - E_act
+  }
+  for (int e = threadIdx.x; e < s * m; e += blockDim.x) Y[(e % s) + (e / s) * ld] = U[e];
+  __syncthreads();
+  const int cap = 6, cap2 = 4;
+  int passes = 0;
+  for (;;) {
+    // C = Y^T X, X <- X - Y C
+    for (int e = threadIdx.x; e < m * a; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      double acc = 0.0;
+      for (int r = 0; r < s; ++r) acc += Y[r + i * ld] * X[r + j * ld];
+      C[i + j * lds] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * a; e += blockDim.x) {
+      const int r = e % s, j = e / s;
+      double acc = 0.0;
+      for (int i = 0; i < m; ++i) acc += Y[r + i * ld] * C[i + j * lds];
+      X[r + j * ld] -= acc;
+    }
+    __syncthreads();
+    small_ortho(s, a, X, ld, tau, cap, M, L, Tm, Z, lds, rot, red, theta, &flag, &shifts);
+    ++passes;
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < m * a; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      double acc = 0.0;
+      for (int r = 0; r < s; ++r) acc += Y[r + i * ld] * X[r + j * ld];
+      const double v = fabs(acc);
+      mx = (v <= mx) ? mx : v;
+      if (v != v) mx = INFINITY;
+    }
+    mx = block_max(mx, red);
+    if (mx <= tau || passes >= cap2) break;
+  }
+  for (int e = threadIdx.x; e < s * a; e += blockDim.x) up[e] = X[(e % s) + (e / s) * ld];
+  if (threadIdx.x == 0) {
+    state->sp_shifts += shifts;
+    state->sp_passes = passes;
+  }
+}
+
+}  // namespace
+
+void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U, int* sweeps_out,
+                 cudaStream_t st) {
+  if (s <= 0) return;
+  if (s > kMaxS) throw std::invalid_argument("syev: s > 96");
+  const size_t smem = (size_t)2 * s * (s + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxS * (kMaxS + 1) * 8));
+    attr = true;
+  }
+  syev_kernel<<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
+  LB_LAUNCH_CHECK();
+}
+
+void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl, cudaStream_t st) {
+  if (p <= 0) return;
+  if (p > kMaxCholP) throw std::invalid_argument("cholqr: p > 64");
+  const size_t smem = (size_t)4 * p * (p + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(cholqr_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kMaxCholP * (kMaxCholP + 1) * 8));
+    attr = true;
+  }
+  cholqr_small_kernel<<<1, kSmallThreads, smem, st>>>(p, M, tau, Linv, ctl);
+  LB_LAUNCH_CHECK();
+}
+
+void launch_maxabs(int count, const double* C, double* out, cudaStream_t st) {
+  maxabs_kernel<<<1, 256, 0, st>>>(count, C, out);
+  LB_LAUNCH_CHECK();
+}
+
+void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, int nparts,
+                       const double* U, double tol, int tol_kind, double tau, LockState* state,
+                       double* resnorm, double* up, bool build_p, cudaStream_t st) {
+  const size_t smem = ((size_t)2 * kMaxM * (kMaxS + 1) + (size_t)5 * kMaxM * (kMaxM + 1)) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(lock_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = true;
+  }
+  lock_p_kernel<<<1, kSmallThreads, smem, st>>>(s, m, k, n, norm_part, nparts, U, tol, tol_kind, tau,
+                                                 state, resnorm, up, build_p ? 1 : 0);
+  LB_LAUNCH_CHECK();
+}
+
+}  // namespace lobpcg

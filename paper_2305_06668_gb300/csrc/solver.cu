@@ -1,0 +1,832 @@
+// Host driver of Algorithm 1 (LOBPCG, Sec. 3.1) with Algorithms 2 and 3 (Sec. 3.2)
+// and the C ABI declared in include/lobpcg.h.
+//
+// The iteration keeps every n-sized block on the GPU in row-major layout:
+//   X, AX, P, AP (double-buffered: the new X and P are built from the old basis), W, AW.
+// The expansion basis is ordered V = [X | P | W] (the paper writes (X, W, P); the order
+// of basis vectors does not change the Rayleigh-Ritz problem, and this order keeps
+// Y = [X | P] contiguous for ortho(W~; Y)).  Small matrices (<= 96 x 96) stay on the
+// GPU in FP64; the host only reads a few flags per step to decide loop exits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/lobpcg.h"
+#include "common.cuh"
+
+using namespace lobpcg;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  void ensure(size_t b) {
+    if (b <= bytes) return;
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    if (b == 0) return;
+    LB_CUDA(cudaMalloc(&p, b));
+    bytes = b;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+  template <class T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+struct InvalidArg : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+struct NoMem : std::runtime_error {
+  using std::runtime_error::runtime_error;
+};
+
+struct Stats {
+  int cholqr_passes_max = 0, ortho_passes_max = 0, shifts = 0, svqb = 0, cap_hits = 0;
+  int64_t spmm_columns = 0;
+};
+
+// Optional per-phase timing with CUDA events recorded on the solver stream.
+enum Phase { PH_SPMM = 0, PH_RR_GRAM, PH_RR_EIG, PH_UPDATE, PH_PRECOND, PH_ORTHO, PH_OTHER, PH_COUNT };
+struct Profiler {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> pool;
+  std::vector<int> phase;
+  size_t used = 0;
+  void begin(bool enable, cudaStream_t s) {
+    on = enable;
+    st = s;
+    used = 0;
+    phase.clear();
+  }
+  void mark(int ph) {
+    if (!on) return;
+    if (used == pool.size()) {
+      cudaEvent_t e;
+      LB_CUDA(cudaEventCreate(&e));
+      pool.push_back(e);
+    }
+    LB_CUDA(cudaEventRecord(pool[used], st));
+    phase.push_back(ph);
+    ++used;
+  }
+  void finish(double* out) {
+    for (int i = 0; i < PH_COUNT; ++i) out[i] = 0.0;
+    if (!on || used < 2) return;
+    LB_CUDA(cudaStreamSynchronize(st));
+    for (size_t i = 0; i + 1 < used; ++i) {
+      float ms = 0.f;
+      LB_CUDA(cudaEventElapsedTime(&ms, pool[i], pool[i + 1]));
+      out[phase[i]] += ms * 1e-3;
+    }
+  }
+  ~Profiler() {
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// Block workspace of one precision.
+template <class T>
+struct Blocks {
+  DevBuf buf;
+  int ld = 0;
+  int64_t n = 0;
+  T *X[2]{}, *AX[2]{}, *P[2]{}, *AP[2]{}, *W = nullptr, *AW = nullptr;
+  void ensure(int64_t n_, int m) {
+    const int vec = 16 / (int)sizeof(T);
+    const int ld_ = round_up(m, vec);
+    const size_t per = (size_t)n_ * ld_ * sizeof(T);
+    buf.ensure(per * 10);
+    n = n_;
+    ld = ld_;
+    T* b = buf.as<T>();
+    const size_t e = (size_t)n_ * ld_;
+    X[0] = b, X[1] = b + e, AX[0] = b + 2 * e, AX[1] = b + 3 * e;
+    P[0] = b + 4 * e, P[1] = b + 5 * e, AP[0] = b + 6 * e, AP[1] = b + 7 * e;
+    W = b + 8 * e, AW = b + 9 * e;
+  }
+};
+
+}  // namespace
+
+struct lobpcg_ctx {
+  lobpcg_matrix A{};
+  lobpcg_options opt{};
+  cudaStream_t st = nullptr;
+  std::string err;
+  int sms = 152;
+  int max_ctas = 304;
+
+  DevBuf val32, dense32;  // FP32 copies for the mixed form
+  Blocks<double> b64;
+  Blocks<float> b32;
+  DevBuf small;  // all small FP64 matrices and partials
+  double *Gpart = nullptr, *G = nullptr, *U = nullptr, *lam_all = nullptr, *up = nullptr;
+  double *Tm = nullptr, *C = nullptr, *npart = nullptr, *resnorm = nullptr, *scal = nullptr;
+  double *lam = nullptr, *sgn = nullptr, *S = nullptr;
+  int* ictl = nullptr;  // [0..3] cholqr ctl, [4] sweeps, [5] finite flag
+  LockState* lock = nullptr;
+  DevBuf x0buf;        // column-major FP64 initial block when X0 == NULL
+  double* host = nullptr;  // pinned readback area
+  Stats stats;
+  Profiler prof;
+  FILE* trace = nullptr;  // per-iteration JSON lines (LOBPCG_TRACE=path)
+
+  void sync() { LB_CUDA(cudaStreamSynchronize(st)); }
+
+  void alloc_small() {
+    const size_t gpart = (size_t)max_ctas * kMaxS * kMaxS;
+    const size_t doubles = gpart + 8 * (size_t)kMaxS * kMaxS + (size_t)max_ctas * 4 * kMaxS + 64 * kMaxS;
+    small.ensure(doubles * sizeof(double) + 4096);
+    double* p = small.as<double>();
+    Gpart = p, p += gpart;
+    G = p, p += kMaxS * kMaxS;
+    U = p, p += kMaxS * kMaxS;
+    up = p, p += kMaxS * kMaxS;
+    Tm = p, p += kMaxS * kMaxS;
+    C = p, p += kMaxS * kMaxS;
+    S = p, p += kMaxS * kMaxS;
+    npart = p, p += (size_t)max_ctas * 4 * kMaxS;
+    lam_all = p, p += kMaxS;
+    lam = p, p += kMaxS;
+    resnorm = p, p += kMaxS;
+    scal = p, p += kMaxS;
+    sgn = p, p += kMaxS;
+    p += 8 * kMaxS;
+    ictl = reinterpret_cast<int*>(p);
+    lock = reinterpret_cast<LockState*>(ictl + 32);
+    LB_CUDA(cudaMallocHost(&host, 64 * kMaxS * sizeof(double)));
+  }
+};
+
+namespace {
+
+// --------------------------------------------------------------------------- helpers
+
+template <class T>
+struct Prec;
+template <>
+struct Prec<double> {
+  static Blocks<double>& blocks(lobpcg_ctx& c) { return c.b64; }
+  static const double* val(lobpcg_ctx& c) { return c.A.val; }
+  static const double* dense(lobpcg_ctx& c) { return c.A.dense; }
+  static int64_t lda(lobpcg_ctx& c) { return c.A.ld; }
+};
+template <>
+struct Prec<float> {
+  static Blocks<float>& blocks(lobpcg_ctx& c) { return c.b32; }
+  static const float* val(lobpcg_ctx& c) { return c.val32.as<float>(); }
+  static const float* dense(lobpcg_ctx& c) { return c.dense32.as<float>(); }
+  static int64_t lda(lobpcg_ctx& c) { return c.A.n; }
+};
+
+template <class T>
+void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
+  if (p <= 0) return;
+  c.prof.mark(PH_SPMM);
+  if (c.A.fmt == LOBPCG_CSR)
+    launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st);
+  else
+    launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
+  c.stats.spmm_columns += p;
+  c.prof.mark(PH_OTHER);
+}
+
+template <class T>
+void gram(lobpcg_ctx& c, const Cols<T>& a, const Cols<T>& b, bool upper, double* out) {
+  const int pa = a.width(), pb = b.width();
+  const int parts = gram_partials<T>(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
+  reduce_partials(c.Gpart, parts, pa * pb, out, c.st);
+}
+
+// W <- W * T (p x p FP64 matrix on device), in place.
+template <class T>
+void right_multiply(lobpcg_ctx& c, T* W, int ld, int p, const double* Tm) {
+  UpdateJob<T> job{};
+  job.in[0] = cols1<T>(W, ld, p);
+  job.out[0] = W;
+  job.ld_out[0] = ld;
+  job.nprod = 1;
+  launch_update<T>(c.A.n, job, Tm, p, p, 1.0, nullptr, nullptr, c.max_ctas, c.st);
+}
+
+// Algorithm 2: W (n x p) <- ortho(W).  Host-driven loop, one flag read per pass.
+template <class T>
+int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap) {
+  if (p <= 0) return 0;
+  int passes = 0;
+  LB_CUDA(cudaMemsetAsync(c.ictl, 0, 4 * sizeof(int), c.st));
+  for (;;) {
+    const Cols<T> w = cols1<T>(W, ld, p);
+    gram<T>(c, w, w, false, c.G);                       // M = W^T W
+    launch_cholqr_small(p, c.G, tau, c.Tm, c.ictl, c.st);  // test ||M - I||, factor
+    LB_CUDA(cudaMemcpyAsync(c.host, c.ictl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    const int* h = reinterpret_cast<const int*>(c.host);
+    if (h[0]) break;
+    if (passes >= cap) {
+      c.stats.cap_hits++;
+      break;
+    }
+    ++passes;
+    right_multiply<T>(c, W, ld, p, c.Tm);               // W <- W L^{-T}
+  }
+  const int* h = reinterpret_cast<const int*>(c.host);
+  c.stats.shifts += h[1];
+  c.stats.svqb += h[2];
+  c.stats.cholqr_passes_max = std::max(c.stats.cholqr_passes_max, passes);
+  return passes;
+}
+
+// Algorithm 3: W (n x p) <- ortho(W; Y), Y orthonormal (Cols).  Body runs at least once.
+template <class T>
+int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double tau, int cap, int cap2) {
+  if (p <= 0) return 0;
+  const int q = Y.width();
+  int passes = 0;
+  c.prof.mark(PH_ORTHO);
+  for (;;) {
+    if (q > 0) {
+      gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);    // C = Y^T W
+      UpdateJob<T> job{};
+      job.in[0] = Y;
+      job.out[0] = W;
+      job.ld_out[0] = ld;
+      job.base[0] = W;
+      job.ld_base[0] = ld;
+      job.nprod = 1;
+      launch_update<T>(c.A.n, job, c.C, q, p, -1.0, nullptr, nullptr, c.max_ctas, c.st);  // W -= Y C
+    }
+    ortho<T>(c, W, ld, p, tau, cap);
+    ++passes;
+    if (q == 0) break;
+    gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);
+    launch_maxabs(q * p, c.C, c.scal, c.st);
+    LB_CUDA(cudaMemcpyAsync(c.host, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    if (c.host[0] <= tau) break;
+    if (passes >= cap2) {
+      c.stats.cap_hits++;
+      break;
+    }
+  }
+  c.stats.ortho_passes_max = std::max(c.stats.ortho_passes_max, passes);
+  c.prof.mark(PH_OTHER);
+  return passes;
+}
+
+template <class T>
+void precondition(lobpcg_ctx& c, const T* X, const T* AX, int ld, int m_conv, int a, T* W) {
+  const int pc = c.opt.precond == LOBPCG_PREC_NONE ? 0 : 1;
+  c.prof.mark(PH_PRECOND);
+  launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st);
+  c.prof.mark(PH_OTHER);
+}
+
+struct PhaseOut {
+  int iterations = 0;
+  int m_conv = 0;
+  bool converged = false;
+  int xbuf = 0;  // which X buffer holds the result
+  std::vector<double> lam, res;
+};
+
+// One run of Algorithm 1 in precision T starting from the row-major block X[0] (n x m,
+// not yet orthonormal).  `stall_exit` enables the mixed-precision switch test.
+template <class T>
+PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int maxiter, bool stall_exit,
+                    double switch_tol = 0.0) {
+  Blocks<T>& b = Prec<T>::blocks(c);
+  const int64_t n = c.A.n;
+  const int ld = b.ld;
+  const int cap = c.opt.ortho_cap, cap2 = c.opt.ortho2_cap;
+  const int tol_kind = c.opt.tol_kind;
+  PhaseOut out;
+  int cur = 0;
+  LockState ls{0, m, 0, 0, 0};
+  LB_CUDA(cudaMemcpyAsync(c.lock, &ls, sizeof ls, cudaMemcpyHostToDevice, c.st));
+
+  auto read_lock = [&](int mm) {
+    LB_CUDA(cudaMemcpyAsync(c.host, c.lock, sizeof(LockState), cudaMemcpyDeviceToHost, c.st));
+    LB_CUDA(cudaMemcpyAsync(c.host + 8, c.resnorm, mm * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    LB_CUDA(cudaMemcpyAsync(c.host + 8 + kMaxS, c.lam_all, mm * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    std::memcpy(&ls, c.host, sizeof ls);
+    out.res.assign(c.host + 8, c.host + 8 + mm);
+    out.lam.assign(c.host + 8 + kMaxS, c.host + 8 + kMaxS + mm);
+  };
+
+  // ---- initialisation ----
+  ortho<T>(c, b.X[0], ld, m, tau, cap);                                 // X0 <- ortho(X0)
+  apply_A<T>(c, b.X[0], ld, m, b.AX[0], ld);                            // AX = A X
+  gram<T>(c, cols1<T>(b.X[0], ld, m), cols1<T>(b.AX[0], ld, m), true, c.G);  // a = X^T AX
+  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st);          // a u = u lambda
+  LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  {
+    UpdateJob<T> job{};
+    job.in[0] = cols1<T>(b.X[0], ld, m);
+    job.in[1] = cols1<T>(b.AX[0], ld, m);
+    job.out[0] = b.X[1], job.out[1] = b.AX[1];
+    job.ld_out[0] = job.ld_out[1] = ld;
+    job.nprod = 2;
+    const int parts = launch_update<T>(n, job, c.U, m, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);
+    launch_lock_and_p(m, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.up,
+                      false, c.st);
+  }
+  cur = 1;
+  read_lock(m);
+  if (ls.done) {
+    out.converged = true;
+    out.m_conv = ls.m_conv;
+    out.xbuf = cur;
+    return out;
+  }
+  int a = ls.m_act, m_conv = ls.m_conv;
+  precondition<T>(c, b.X[cur], b.AX[cur], ld, m_conv, a, b.W);         // W~ = T R
+  ortho_against<T>(c, b.W, ld, a, cols1<T>(b.X[cur], ld, m), tau, cap, cap2);  // W = ortho(W~; X)
+  apply_A<T>(c, b.W, ld, a, b.AW, ld);                                  // AW = A W
+  int pw = 0;  // width of P in the current basis
+  double best_rk = 1e300;
+  int since_best = 0;
+
+  // ---- main loop ----
+  int it = 1;
+  for (; it <= maxiter; ++it) {
+    const int s = m + pw + a;
+    Cols<T> V = cols1<T>(b.X[cur], ld, m);
+    V = cols_add<T>(V, b.P[cur], ld, pw);
+    V = cols_add<T>(V, b.W, ld, a);
+    Cols<T> AV = cols1<T>(b.AX[cur], ld, m);
+    AV = cols_add<T>(AV, b.AP[cur], ld, pw);
+    AV = cols_add<T>(AV, b.AW, ld, a);
+    c.prof.mark(PH_RR_GRAM);
+    gram<T>(c, V, AV, true, c.G);                                       // a = V^T AV (upper)
+    c.prof.mark(PH_RR_EIG);
+    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st);        // Rayleigh-Ritz
+    c.prof.mark(PH_UPDATE);
+    LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    const int nxt = cur ^ 1;
+    UpdateJob<T> job{};
+    job.in[0] = V, job.in[1] = AV;
+    job.out[0] = b.X[nxt], job.out[1] = b.AX[nxt];
+    job.ld_out[0] = job.ld_out[1] = ld;
+    job.nprod = 2;
+    const int parts = launch_update<T>(n, job, c.U, s, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);  // X = V u_x
+    launch_lock_and_p(s, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.up,
+                      true, c.st);                                      // lock, u_p
+    read_lock(m);
+    c.prof.mark(PH_OTHER);
+    if (c.trace) {
+      std::fprintf(c.trace, "{\"it\": %d, \"prec\": %d, \"s\": %d, \"m_act\": %d, \"lambda\": [", it,
+                   (int)sizeof(T) * 8, s, ls.m_act);
+      for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.17g", j ? ", " : "", out.lam[j]);
+      std::fprintf(c.trace, "], \"res\": [");
+      for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.6e", j ? ", " : "", out.res[j]);
+      std::fprintf(c.trace, "]}\n");
+    }
+    if (ls.done) {
+      cur = nxt;
+      out.converged = true;
+      break;
+    }
+    if (stall_exit) {
+      // mixed-precision switch: leave this precision once every one of the k sought
+      // residuals is below switch_tol, or (switch_tol == 0) once the largest of them has
+      // not improved by 10% for 5 iterations (its rounding floor)
+      double rk = 0.0;
+      for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
+      if (switch_tol > 0.0) {
+        if (rk <= switch_tol) {
+          cur = nxt;
+          break;
+        }
+      } else if (rk < 0.9 * best_rk) {
+        best_rk = rk, since_best = 0;
+      } else if (++since_best >= 5) {
+        cur = nxt;
+        break;
+      }
+    }
+    const int a_new = ls.m_act;
+    m_conv = ls.m_conv;
+    c.prof.mark(PH_UPDATE);
+    {
+      UpdateJob<T> pj{};
+      pj.in[0] = V, pj.in[1] = AV;
+      pj.out[0] = b.P[nxt], pj.out[1] = b.AP[nxt];
+      pj.ld_out[0] = pj.ld_out[1] = ld;
+      pj.nprod = 2;
+      launch_update<T>(n, pj, c.up, s, a_new, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // P = V u_p
+    }
+    c.prof.mark(PH_OTHER);
+    cur = nxt;
+    a = a_new;
+    pw = a;
+    precondition<T>(c, b.X[cur], b.AX[cur], ld, m_conv, a, b.W);       // W~ = T R
+    Cols<T> Y = cols1<T>(b.X[cur], ld, m);
+    Y = cols_add<T>(Y, b.P[cur], ld, a);
+    ortho_against<T>(c, b.W, ld, a, Y, tau, cap, cap2);                 // W = ortho(W~; (X, P))
+    apply_A<T>(c, b.W, ld, a, b.AW, ld);                                // AW = A W
+  }
+  out.iterations = std::min(it, maxiter);
+  out.m_conv = ls.m_conv;
+  out.xbuf = cur;
+  return out;
+}
+
+lobpcg_status fail(lobpcg_ctx* c, lobpcg_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return s;
+}
+
+template <class F>
+lobpcg_status guarded(lobpcg_ctx* c, F&& f) {
+  try {
+    return f();
+  } catch (const InvalidArg& e) {
+    return fail(c, LOBPCG_EINVAL, e.what());
+  } catch (const NoMem& e) {
+    return fail(c, LOBPCG_ENOMEM, e.what());
+  } catch (const CudaError& e) {
+    const std::string w = e.what();
+    const bool oom = w.find("out of memory") != std::string::npos;
+    return fail(c, oom ? LOBPCG_ENOMEM : LOBPCG_ECUDA, w);
+  } catch (const std::invalid_argument& e) {
+    return fail(c, LOBPCG_EINVAL, e.what());
+  } catch (const std::bad_alloc& e) {
+    return fail(c, LOBPCG_ENOMEM, e.what());
+  } catch (const std::exception& e) {
+    return fail(c, LOBPCG_ECUDA, e.what());
+  } catch (...) {
+    return fail(c, LOBPCG_ECUDA, "unknown error");
+  }
+}
+
+void require(bool ok, const char* what) {
+  if (!ok) throw InvalidArg(what);
+}
+
+}  // namespace
+
+// ===================================================================== C ABI
+
+extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
+  if (!opt) return LOBPCG_EINVAL;
+  std::memset(opt, 0, sizeof *opt);
+  opt->extra = 0;
+  opt->maxiter = 1000;
+  opt->tol_kind = 0;
+  opt->precond = LOBPCG_PREC_DIAG;
+  opt->precision = LOBPCG_FP64;
+  opt->tau_ortho = 1e-14;
+  opt->ortho_cap = 6;
+  opt->ortho2_cap = 4;
+  opt->seed = 0;
+  opt->mlp_weights = nullptr;
+  return LOBPCG_OK;
+}
+
+extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
+                                       const lobpcg_options* opt, lobpcg_stream stream) {
+  if (out) *out = nullptr;
+  std::unique_ptr<lobpcg_ctx> c(new (std::nothrow) lobpcg_ctx());
+  if (!c) return fail(nullptr, LOBPCG_ENOMEM, "host allocation failed");
+  lobpcg_status st = guarded(nullptr, [&]() -> lobpcg_status {
+    require(out && A, "lobpcg_create: out and A must not be NULL");
+    require(A->n >= 3, "lobpcg_create: n must be >= 3");
+    require(A->diag != nullptr, "lobpcg_create: diag must not be NULL");
+    if (A->fmt == LOBPCG_CSR)
+      require(A->row_ptr && A->col_idx && A->val && A->nnz >= 0, "lobpcg_create: CSR arrays missing");
+    else if (A->fmt == LOBPCG_DENSE)
+      require(A->dense && A->ld >= A->n, "lobpcg_create: dense array missing or ld < n");
+    else
+      throw InvalidArg("lobpcg_create: unknown format");
+    c->A = *A;
+    if (opt) c->opt = *opt;
+    else lobpcg_options_default(&c->opt);
+    if (c->opt.maxiter <= 0) c->opt.maxiter = 1000;
+    if (!(c->opt.tau_ortho > 0)) c->opt.tau_ortho = 1e-14;
+    if (c->opt.ortho_cap <= 0) c->opt.ortho_cap = 6;
+    if (c->opt.ortho2_cap <= 0) c->opt.ortho2_cap = 4;
+    require(c->opt.extra >= 0, "lobpcg_create: extra must be >= 0");
+    require(c->opt.tol_kind == 0 || c->opt.tol_kind == 1, "lobpcg_create: tol_kind must be 0 or 1");
+    require(c->opt.precond >= LOBPCG_PREC_NONE && c->opt.precond <= LOBPCG_PREC_LEARNED,
+            "lobpcg_create: unknown preconditioner");
+    require(c->opt.precision == LOBPCG_FP64 || c->opt.precision == LOBPCG_MIXED,
+            "lobpcg_create: unknown precision");
+    require(c->opt.precond != LOBPCG_PREC_LEARNED || c->opt.mlp_weights,
+            "lobpcg_create: learned preconditioner needs mlp_weights");
+    c->st = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0;
+    LB_CUDA(cudaGetDevice(&dev));
+    LB_CUDA(cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, dev));
+    c->max_ctas = 2 * c->sms;
+    c->alloc_small();
+    // reject non-finite matrix entries (a host-visible error instead of NaN results)
+    LB_CUDA(cudaMemsetAsync(c->ictl + 5, 0xff, sizeof(int), c->st));
+    const int one = 1;
+    LB_CUDA(cudaMemcpyAsync(c->ictl + 5, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    if (A->fmt == LOBPCG_CSR) launch_all_finite(A->nnz, A->val, c->ictl + 5, c->st);
+    else if (A->ld == A->n) launch_all_finite(A->n * A->n, A->dense, c->ictl + 5, c->st);
+    else for (int64_t j = 0; j < A->n; ++j) launch_all_finite(A->n, A->dense + j * A->ld, c->ictl + 5, c->st);
+    launch_all_finite(A->n, A->diag, c->ictl + 5, c->st);
+    int finite = 0;
+    LB_CUDA(cudaMemcpyAsync(&finite, c->ictl + 5, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    c->sync();
+    require(finite == 1, "lobpcg_create: matrix or diagonal has non-finite entries");
+    if (c->opt.precision == LOBPCG_MIXED) {
+      if (A->fmt == LOBPCG_CSR) {
+        c->val32.ensure((size_t)std::max<int64_t>(A->nnz, 1) * sizeof(float));
+        launch_to_float(A->nnz, A->val, c->val32.as<float>(), c->st);
+      } else {
+        c->dense32.ensure((size_t)A->n * A->n * sizeof(float));
+        if (A->ld == A->n) launch_to_float(A->n * A->n, A->dense, c->dense32.as<float>(), c->st);
+        else for (int64_t j = 0; j < A->n; ++j)
+          launch_to_float(A->n, A->dense + j * A->ld, c->dense32.as<float>() + j * A->n, c->st);
+      }
+    }
+    require(c->opt.precond != LOBPCG_PREC_LEARNED, "lobpcg_create: learned preconditioner not built");
+    c->opt.mlp_weights = nullptr;  // not retained
+    c->sync();
+    return LOBPCG_OK;
+  });
+  if (st == LOBPCG_OK) *out = c.release();
+  return st;
+}
+
+extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const double* X0,
+                                      double* evals, double* evecs, double* resnorms,
+                                      lobpcg_info* info) {
+  if (!c) return fail(nullptr, LOBPCG_EINVAL, "lobpcg_solve: NULL context");
+  return guarded(c, [&]() -> lobpcg_status {
+    const int64_t n = c->A.n;
+    const int m = k + c->opt.extra;
+    require(k >= 1, "lobpcg_solve: k must be >= 1");
+    require(m <= kMaxM, "lobpcg_solve: k + extra must be <= 32");
+    require(3 * (int64_t)m <= n, "lobpcg_solve: 3 (k + extra) must be <= n");
+    require(tol > 0 && std::isfinite(tol), "lobpcg_solve: tol must be positive");
+    require(evals && evecs && resnorms, "lobpcg_solve: output pointers must not be NULL");
+    c->stats = Stats{};
+    c->prof.begin(c->opt.profile != 0, c->st);
+    const char* tr = std::getenv("LOBPCG_TRACE");
+    c->trace = tr && *tr ? std::fopen(tr, "a") : nullptr;
+    cudaEvent_t e0, e1;
+    LB_CUDA(cudaEventCreate(&e0));
+    LB_CUDA(cudaEventCreate(&e1));
+    LB_CUDA(cudaEventRecord(e0, c->st));
+    c->b64.ensure(n, m);
+    const double* x0 = X0;
+    if (!x0) {
+      c->x0buf.ensure((size_t)n * m * sizeof(double));
+      launch_gaussian(n, m, c->opt.seed, c->x0buf.as<double>(), c->st);
+      x0 = c->x0buf.as<double>();
+    } else {
+      const int one = 1;
+      LB_CUDA(cudaMemcpyAsync(c->ictl + 5, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+      launch_all_finite(n * m, X0, c->ictl + 5, c->st);
+      int finite = 0;
+      LB_CUDA(cudaMemcpyAsync(&finite, c->ictl + 5, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+      c->sync();
+      require(finite == 1, "lobpcg_solve: X0 has non-finite entries");
+    }
+    int iters = 0, fp64_iters = 0;
+    PhaseOut ph;
+    const double tau = c->opt.tau_ortho;
+    if (c->opt.precision == LOBPCG_MIXED) {
+      c->b32.ensure(n, m);
+      launch_colmajor_to_rows<double, float>(n, m, x0, c->b32.X[0], c->b32.ld, c->st);
+      const double tau32 = std::max(tau, 3e-5);
+      PhaseOut p32 = run_lobpcg<float>(*c, k, m, tol, tau32, c->opt.maxiter, true, c->opt.mixed_switch);
+      iters += p32.iterations;
+      // continue in FP64 from the FP32 block
+      Blocks<float>& b = c->b32;
+      c->x0buf.ensure((size_t)n * m * sizeof(double));
+      launch_rows_to_colmajor<float, double>(n, m, b.X[p32.xbuf], b.ld, c->x0buf.as<double>(), c->st);
+      launch_colmajor_to_rows<double, double>(n, m, c->x0buf.as<double>(), c->b64.X[0], c->b64.ld, c->st);
+      ph = run_lobpcg<double>(*c, k, m, tol, tau, std::max(1, c->opt.maxiter - p32.iterations), false);
+      fp64_iters = ph.iterations;
+      iters += ph.iterations;
+    } else {
+      launch_colmajor_to_rows<double, double>(n, m, x0, c->b64.X[0], c->b64.ld, c->st);
+      ph = run_lobpcg<double>(*c, k, m, tol, tau, c->opt.maxiter, false);
+      iters = fp64_iters = ph.iterations;
+    }
+    // ---- outputs: normalise, fix signs, fresh residuals ----
+    Blocks<double>& b = c->b64;
+    const double* X = b.X[ph.xbuf];
+    const Cols<double> xk = cols1<double>(X, b.ld, k);
+    gram<double>(*c, xk, xk, false, c->G);
+    launch_col_sign<double>(n, k, X, b.ld, c->Gpart, c->max_ctas, c->sgn, c->st);
+    launch_scale_matrix(k, c->G, c->sgn, c->S, c->st);
+    double* Xs = b.P[0];   // scratch blocks (no longer needed)
+    double* AXs = b.AP[0];
+    {
+      UpdateJob<double> job{};
+      job.in[0] = cols1<double>(X, b.ld, k);
+      job.out[0] = Xs;
+      job.ld_out[0] = b.ld;
+      job.nprod = 1;
+      launch_update<double>(n, job, c->S, k, k, 1.0, nullptr, nullptr, c->max_ctas, c->st);
+    }
+    apply_A<double>(*c, Xs, b.ld, k, AXs, b.ld);
+    c->stats.spmm_columns -= k;  // the check product is not part of the iteration
+    {
+      // residual norms of the normalised vectors: out = in * I (reuse the update epilogue)
+      std::vector<double> eye((size_t)k * k, 0.0);
+      for (int j = 0; j < k; ++j) eye[(size_t)j * k + j] = 1.0;
+      LB_CUDA(cudaMemcpyAsync(c->Tm, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      UpdateJob<double> job{};
+      job.in[0] = cols1<double>(Xs, b.ld, k);
+      job.in[1] = cols1<double>(AXs, b.ld, k);
+      job.out[0] = b.W, job.out[1] = b.AW;
+      job.ld_out[0] = job.ld_out[1] = b.ld;
+      job.nprod = 2;
+      const int parts = launch_update<double>(n, job, c->Tm, k, k, 1.0, c->lam, c->npart, c->max_ctas, c->st);
+      LockState tmp{0, k, 0, 0, 0};
+      LB_CUDA(cudaMemcpyAsync(c->lock, &tmp, sizeof tmp, cudaMemcpyHostToDevice, c->st));
+      launch_lock_and_p(k, k, k, n, c->npart, parts, c->Tm, tol, 0, tau, c->lock, c->resnorm, c->up, false, c->st);
+    }
+    launch_rows_to_colmajor<double, double>(n, k, Xs, b.ld, evecs, c->st);
+    LB_CUDA(cudaMemcpyAsync(evals, c->lam, k * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    LB_CUDA(cudaMemcpyAsync(resnorms, c->resnorm, k * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    LB_CUDA(cudaEventRecord(e1, c->st));
+    c->sync();
+    float ms = 0.f;
+    LB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    double phases[PH_COUNT];
+    c->prof.finish(phases);
+    if (c->trace) std::fclose(c->trace);
+    c->trace = nullptr;
+    if (info) {
+      info->iterations = iters;
+      info->fp64_iterations = fp64_iters;
+      info->converged = ph.m_conv;
+      info->cholqr_passes_max = c->stats.cholqr_passes_max;
+      info->ortho_passes_max = c->stats.ortho_passes_max;
+      info->shifts = c->stats.shifts;
+      info->svqb = c->stats.svqb;
+      info->cap_hits = c->stats.cap_hits;
+      info->spmm_columns = c->stats.spmm_columns;
+      info->seconds = ms * 1e-3;
+      for (int i = 0; i < 6; ++i) info->phase_seconds[i] = phases[i];
+    }
+    for (int j = 0; j < k; ++j)
+      if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))
+        return fail(c, LOBPCG_EBREAKDOWN, "lobpcg_solve: non-finite result (basis breakdown)");
+    if (!ph.converged) return fail(c, LOBPCG_ENOCONV, "lobpcg_solve: maxiter reached before convergence");
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->st);
+  c->val32.release();
+  c->dense32.release();
+  c->b64.buf.release();
+  c->b32.buf.release();
+  c->small.release();
+  c->x0buf.release();
+  if (c->host) cudaFreeHost(c->host);
+  delete c;
+}
+
+extern "C" const char* lobpcg_last_error(const lobpcg_ctx* c) {
+  if (!c) return g_create_error.c_str();
+  return c->err.c_str();
+}
+
+// ============================================================ building-block entry points
+
+namespace {
+// A context without a matrix: workspace for the block-level entry points.
+struct ScratchCtx {
+  lobpcg_ctx c;
+  ScratchCtx(int64_t n, cudaStream_t st) {
+    c.A.n = n;
+    c.st = st;
+    int dev = 0;
+    LB_CUDA(cudaGetDevice(&dev));
+    LB_CUDA(cudaDeviceGetAttribute(&c.sms, cudaDevAttrMultiProcessorCount, dev));
+    c.max_ctas = 2 * c.sms;
+    lobpcg_options_default(&c.opt);
+    c.alloc_small();
+  }
+  ~ScratchCtx() {
+    c.small.release();
+    if (c.host) cudaFreeHost(c.host);
+    c.host = nullptr;
+  }
+};
+}  // namespace
+
+extern "C" lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                             const double* val, int p, const double* X, int ldx,
+                                             double* Y, int ldy, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 0 && row_ptr && col_idx && val && X && Y, "lobpcg_spmm_csr_f64: NULL argument");
+    require(p >= 1 && p <= 32 && ldx >= p && ldy >= p, "lobpcg_spmm_csr_f64: need 1 <= p <= 32, ld >= p");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    launch_spmm_csr<double, double>(n, row_ptr, col_idx, val, p, X, ldx, Y, ldy, st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64_t lda, int p,
+                                               const double* X, int ldx, double* Y, int ldy,
+                                               lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 0 && A && X && Y && lda >= n, "lobpcg_spmm_dense_f64: NULL argument or lda < n");
+    require(p >= 1 && p <= 32 && ldx >= p && ldy >= p, "lobpcg_spmm_dense_f64: need 1 <= p <= 32, ld >= p");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    launch_spmm_dense<double>(n, A, lda, p, X, ldx, Y, ldy, st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int ldx, int q,
+                                         const double* Y, int ldy, double* C, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && X && Y && C, "lobpcg_gram_f64: NULL argument or n < 1");
+    require(p >= 1 && q >= 1 && p <= kMaxS && q <= kMaxS && ldx >= p && ldy >= q,
+            "lobpcg_gram_f64: need 1 <= p, q <= 96, ld >= width");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    gram<double>(s.c, cols1<double>(X, ldx, p), cols1<double>(Y, ldy, q), false, C);
+    s.c.sync();
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U,
+                                         lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(s >= 1 && s <= kMaxS && a && lam && U, "lobpcg_syev_f64: need 1 <= s <= 96 and non-NULL arrays");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    launch_syev(s, a, false, lam, U, nullptr, st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_ortho_f64(int64_t n, int p, double* X, int ldx, double tau, int cap,
+                                          int* stats, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= p && p >= 1 && p <= kMaxM && X && ldx >= p, "lobpcg_ortho_f64: need 1 <= p <= min(32, n)");
+    require(tau > 0 && cap >= 1, "lobpcg_ortho_f64: tau > 0 and cap >= 1 required");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    const int passes = ortho<double>(s.c, X, ldx, p, tau, cap);
+    s.c.sync();
+    if (stats) {
+      stats[0] = passes;
+      stats[1] = s.c.stats.shifts;
+      stats[2] = s.c.stats.svqb;
+      stats[3] = s.c.stats.cap_hits;
+    }
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_ortho_against_f64(int64_t n, int p, double* X, int ldx, int q,
+                                                  const double* Y, int ldy, double tau, int cap,
+                                                  int cap2, int* stats, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= p + q && p >= 1 && p <= kMaxM && q >= 0 && q <= 2 * kMaxM && X && ldx >= p,
+            "lobpcg_ortho_against_f64: need 1 <= p <= 32, 0 <= q <= 64, p + q <= n");
+    require(q == 0 || (Y && ldy >= q), "lobpcg_ortho_against_f64: Y missing or ldy < q");
+    require(tau > 0 && cap >= 1 && cap2 >= 1, "lobpcg_ortho_against_f64: tau > 0 and caps >= 1 required");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    const int passes = ortho_against<double>(s.c, X, ldx, p, cols1<double>(Y, ldy, q), tau, cap, cap2);
+    s.c.sync();
+    if (stats) {
+      stats[0] = passes;
+      stats[1] = s.c.stats.cholqr_passes_max;
+      stats[2] = s.c.stats.shifts;
+      stats[3] = s.c.stats.svqb;
+      stats[4] = s.c.stats.cap_hits;
+    }
+    return LOBPCG_OK;
+  });
+}

@@ -134,11 +134,16 @@ def dense_casscf(n: int = 8192, seed: int = 0, rank: int = 256) -> tuple[np.ndar
 def diag_guess(diag: np.ndarray, m: int, seed: int, noise: float = 1e-3) -> np.ndarray:
     """Initial block: unit vectors at the m smallest diagonal entries plus N(0, noise^2).
 
-    Returned as an n x m column-major (Fortran-ordered) float64 array.
+    Returned as an n x m column-major (Fortran-ordered) float64 array.  noise=0 gives the
+    plain unit-vector guess used for the large CI-like matrices, where per-entry noise
+    over millions of rows would dominate the Rayleigh quotient.
     """
     n = diag.shape[0]
     g = rng(seed, 4)
-    x = g.normal(0.0, noise, size=(m, n)).T.copy(order="F")
+    if noise > 0:
+        x = g.normal(0.0, noise, size=(m, n)).T.copy(order="F")
+    else:
+        x = np.zeros((n, m), order="F")
     idx = np.argsort(diag, kind="stable")[:m]
     x[idx, np.arange(m)] += 1.0
     return x

@@ -1,0 +1,46 @@
+"""CPU-side checks of the compiled library: it loads and exports every C entry point."""
+import ctypes
+import re
+import subprocess
+
+import pytest
+
+import paper_2305_06668_gb300 as lb
+from paper_2305_06668_gb300 import build as gpu_build
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    return gpu_build.build()
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    declared = lb.exported_symbols()
+    assert "lobpcg_create" in declared and "lobpcg_solve" in declared and "lobpcg_destroy" in declared
+    out = subprocess.run(["nm", "-D", "--defined-only", str(libpath)], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT (lobpcg_\w+)", out))
+    missing = [s for s in declared if s not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_errors_without_gpu(libpath):
+    L = lb.lib()
+    o = lb._Options()
+    assert L.lobpcg_options_default(ctypes.byref(o)) == lb.OK
+    assert o.maxiter == 1000 and o.tau_ortho == 1e-14 and o.precond == lb.PREC_DIAG
+    assert L.lobpcg_options_default(None) == lb.EINVAL
+    # NULL arguments are rejected before any device work
+    ctx = ctypes.c_void_p()
+    assert L.lobpcg_create(ctypes.byref(ctx), None, None, None) == lb.EINVAL
+    assert b"NULL" in L.lobpcg_last_error(None)
+    assert L.lobpcg_solve(None, 1, ctypes.c_double(1e-8), None, None, None, None, None) == lb.EINVAL
+    L.lobpcg_destroy(None)  # NULL-safe
+
+
+def test_no_cpu_fallback_in_product_package():
+    import pathlib
+    pkg = pathlib.Path(lb.__file__).parent
+    for f in list(pkg.glob("*.py")) + list((pkg / "csrc").glob("*")):
+        text = f.read_text()
+        assert "import oracle" not in text and "from oracle" not in text, f
+        assert "lobpcg_oracle" not in text, f

@@ -1,0 +1,121 @@
+"""GPU building blocks (through the C ABI) against the CPU oracle, element by element."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import cuda, dev
+from tests.util import max_subspace_angle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n,p", [(1, 1), (97, 3), (4096, 4), (20011, 16), (5003, 32), (3001, 7)])
+def test_spmm_csr_matches_oracle(n, p):
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_cfg1(n=max(n, 3), seed=n) if n >= 3 else synth.tridiag_toeplitz(3, 1.0, 0.5)
+    n = a.n
+    X = synth.gaussian_block(n, p, seed=1)
+    t = lb.upload_csr(a)
+    Y = lb.spmm_csr(t["row_ptr"], t["col_idx"], t["val"], dev(torch, X)).cpu().numpy()
+    ref = oracle.apply(a, X)
+    scale = np.abs(a.to_scipy()) @ np.abs(X)
+    assert np.all(np.abs(Y - ref) <= 4 * np.finfo(float).eps * 64 * (scale + 1e-300))
+
+
+def test_spmm_csr_ci_band_matrix_ragged_tail():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=50_001, seed=4)
+    X = synth.gaussian_block(a.n, 16, seed=2)
+    t = lb.upload_csr(a)
+    Y = lb.spmm_csr(t["row_ptr"], t["col_idx"], t["val"], dev(torch, X)).cpu().numpy()
+    ref = oracle.apply(a, X)
+    scale = np.abs(a.to_scipy()) @ np.abs(X)
+    assert np.all(np.abs(Y - ref) <= 4 * np.finfo(float).eps * 80 * scale)
+
+
+@pytest.mark.parametrize("n,p", [(300, 4), (1031, 8), (2048, 13)])
+def test_spmm_dense_matches_oracle(n, p):
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(n)
+    B = g.standard_normal((n, n))
+    A = np.asfortranarray(B + B.T)
+    X = synth.gaussian_block(n, p, seed=3)
+    Y = lb.spmm_dense(torch.from_numpy(A).cuda(), dev(torch, X)).cpu().numpy()
+    ref = oracle.apply(A, X)
+    scale = np.abs(A) @ np.abs(X)
+    assert np.all(np.abs(Y - ref) <= 4 * np.finfo(float).eps * n * scale)
+
+
+@pytest.mark.parametrize("n,p,q", [(1, 1, 1), (33, 5, 3), (10007, 16, 16), (100003, 48, 48), (4099, 96, 40), (777, 96, 96)])
+def test_gram_matches_oracle(n, p, q):
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    X = synth.gaussian_block(n, p, seed=5)
+    Y = synth.gaussian_block(n, q, seed=6)
+    Cg = lb.gram(dev(torch, X), dev(torch, Y)).cpu().numpy()
+    ref = oracle.gram(X, Y)
+    scale = np.abs(X).T @ np.abs(Y)
+    assert np.all(np.abs(Cg - ref) <= 8 * np.finfo(float).eps * np.log2(n + 2) * 16 * scale + 1e-300)
+
+
+@pytest.mark.parametrize("s", [1, 2, 5, 12, 48, 95, 96])
+def test_syev_matches_oracle_jacobi(s):
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(s)
+    a = g.standard_normal((s, s))
+    a = 0.5 * (a + a.T)
+    lam, U = lb.syev(torch.from_numpy(a).cuda())
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    lr, Ur, _ = oracle.jacobi_eig(a)
+    nrm = max(1.0, np.linalg.norm(a))
+    assert np.max(np.abs(lam - lr)) <= 1e-13 * nrm
+    assert np.max(np.abs(U.T @ U - np.eye(s))) <= 1e-13 * s
+    for j in range(s):  # simple eigenvalues: vectors agree up to sign
+        assert abs(abs(U[:, j] @ Ur[:, j]) - 1) <= 1e-10
+
+
+def test_ortho_matches_oracle_cholqr():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(7)
+    X = g.standard_normal((30011, 12)) @ np.diag(10.0 ** np.linspace(0, 6, 12))
+    Q, st = lb.ortho(dev(torch, X))
+    Q = Q.cpu().numpy()
+    Qr, str_ = oracle.ortho(np.asfortranarray(X))
+    assert np.max(np.abs(Q.T @ Q - np.eye(12))) <= 1e-14
+    assert np.max(np.abs(Q - Qr)) <= 1e-11
+    assert st["passes"] == str_["passes"]
+
+
+def test_ortho_shifted_path():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(3)
+    U, _ = np.linalg.qr(g.standard_normal((3000, 8)))
+    Vt, _ = np.linalg.qr(g.standard_normal((8, 8)))
+    X = U @ np.diag(np.logspace(0, -12, 8)) @ Vt
+    Q, st = lb.ortho(dev(torch, X))
+    Q = Q.cpu().numpy()
+    assert st["shifts"] >= 1 and st["passes"] <= 4
+    assert np.max(np.abs(Q.T @ Q - np.eye(8))) <= 1e-14
+    assert max_subspace_angle(Q, U) < 1e-3
+
+
+def test_ortho_against_matches_properties_and_oracle():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(5)
+    Y, _ = np.linalg.qr(g.standard_normal((40000, 20)))
+    Xt = Y @ g.standard_normal((20, 6)) + 1e-9 * g.standard_normal((40000, 6))
+    Q, st = lb.ortho_against(dev(torch, Xt), dev(torch, Y))
+    Q = Q.cpu().numpy()
+    Qr, str_ = oracle.ortho_against(np.asfortranarray(Xt), np.asfortranarray(Y))
+    assert np.max(np.abs(Y.T @ Q)) <= 1e-14
+    assert np.max(np.abs(Q.T @ Q - np.eye(6))) <= 1e-14
+    assert max_subspace_angle(Q, Qr) <= 1e-6
+    assert st["passes"] >= 2

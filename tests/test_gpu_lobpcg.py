@@ -1,0 +1,157 @@
+"""The full GPU solver (C ABI) against the CPU oracle on the same seeded inputs.
+
+Bar: |d lambda| <= 1e-10 max(1, |lambda|), largest principal angle <= 1e-7 per cluster
+of eigenvalues closer than 1e-8 max(1, |lambda|)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import cuda, dev
+from tests.util import cluster_angles, rel_eig_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _solve(torch, a, k, x0, dense=None, **kw):
+    import paper_2305_06668_gb300 as lb
+    tol = kw.pop("tol", 1e-8)
+    if dense is not None:
+        s = lb.Solver(diag=dev(torch, np.diag(dense).copy()), dense=torch.from_numpy(np.asfortranarray(dense)).cuda(), **kw)
+    else:
+        s = lb.Solver(**lb.upload_csr(a), **kw)
+    r = s.solve(k, tol, X0=None if x0 is None else torch.from_numpy(x0).cuda())
+    s.close()
+    return r
+
+
+def _parity(res, ref, lam_ref=None):
+    lam_ref = ref.evals if lam_ref is None else lam_ref
+    assert np.max(rel_eig_err(res.evals, lam_ref)) <= 1e-10
+    V = res.evecs.cpu().numpy()
+    assert np.max(cluster_angles(lam_ref, ref.evecs, V)) <= 1e-7
+
+
+@pytest.mark.parametrize("n,k,seed,noise", [(4096, 4, 0, 1e-3), (5003, 3, 1, 1e-3), (20011, 8, 2, 0.0)])
+def test_fp64_matches_oracle_sparse(n, k, seed, noise):
+    # noise 1e-3 per entry on n = 20011 rows would put ~2 units of Rayleigh quotient in
+    # the noise and let both solvers settle on non-lowest pairs; the unit-vector guess
+    # is used there
+    torch = cuda()
+    a = synth.sparse_cfg1(n=n, seed=seed)
+    x0 = synth.diag_guess(a.diag, k, seed=seed, noise=noise)
+    ref = oracle.lobpcg(a, a.diag, k, x0, tol=1e-8)
+    res = _solve(torch, a, k, x0)
+    assert ref.status == 0 and res.status == 0
+    _parity(res, ref)
+    assert np.max(res.resnorms) <= 1e-8
+    # On this recipe the iteration count is chaotic: perturbing X0 by 1e-15 moves the
+    # oracle's own count between about 50 and 190, so only a loose bound is checked.
+    assert res.info["iterations"] <= 4 * ref.info["iterations"] + 50
+
+
+def test_fp64_ci_band_matrix():
+    torch = cuda()
+    a = synth.sparse_ci(n=60_001, seed=5)
+    k = 6
+    x0 = synth.diag_guess(a.diag, k, seed=5, noise=0.0)
+    ref = oracle.lobpcg(a, a.diag, k, x0, tol=1e-8)
+    res = _solve(torch, a, k, x0)
+    assert ref.status == 0 and res.status == 0
+    _parity(res, ref)
+    assert abs(res.info["iterations"] - ref.info["iterations"]) <= max(3, 0.15 * ref.info["iterations"])
+
+
+def test_fp64_dense_ill_conditioned():
+    torch = cuda()
+    A, d = synth.dense_casscf(n=1024, seed=2, rank=64)
+    k = 4
+    x0 = synth.diag_guess(d, k, seed=2)
+    ref = oracle.lobpcg(A, d, k, x0, tol=1e-8, maxiter=3000)
+    res = _solve(torch, None, k, x0, dense=A, maxiter=3000)
+    assert ref.status == 0 and res.status == 0
+    w = np.linalg.eigvalsh(A)[:k]
+    assert np.max(rel_eig_err(ref.evals, w)) <= 1e-10
+    _parity(res, ref)
+
+
+def test_fp64_extra_columns_and_rms_criterion():
+    torch = cuda()
+    a = synth.sparse_cfg1(n=3001, seed=9)
+    x0 = synth.diag_guess(a.diag, 5, seed=9)
+    ref = oracle.lobpcg(a, a.diag, 3, x0, tol=1e-8, extra=2, tol_kind=1)
+    res = _solve(torch, a, 3, x0, extra=2, tol_kind=1)
+    assert ref.status == 0 and res.status == 0
+    _parity(res, ref)
+
+
+def test_fp64_exact_start_exits_after_init():
+    torch = cuda()
+    d = np.array([5.0, 0.5, 3.0, -1.0, 2.0, 7.0, 0.0, 4.0, 6.0, 1.5, 9.0, 8.0])
+    A = np.diag(d)
+    idx = np.argsort(d)[:3]
+    x0 = np.asfortranarray(np.eye(12)[:, idx])
+    res = _solve(torch, None, 3, x0, dense=A)
+    assert res.status == 0 and res.info["iterations"] == 0
+    assert np.array_equal(res.evals, np.sort(d)[:3])
+    assert np.array_equal(res.evecs.cpu().numpy(), x0)
+    assert np.all(res.resnorms == 0)
+
+
+def test_fp64_random_start_finds_same_eigenpairs():
+    torch = cuda()
+    a = synth.sparse_cfg1(n=2000, seed=4)
+    k = 3
+    ref = oracle.lobpcg(a, a.diag, k, synth.diag_guess(a.diag, k, seed=4), tol=1e-9)
+    res = _solve(torch, a, k, None, seed=123, tol=1e-9)
+    assert res.status == 0
+    _parity(res, ref)
+
+
+def test_noconv_and_invalid_arguments():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_cfg1(n=2000, seed=2)
+    x0 = synth.diag_guess(a.diag, 2, seed=1)
+    res = _solve(torch, a, 2, x0, maxiter=2)
+    ref = oracle.lobpcg(a, a.diag, 2, x0, maxiter=2)
+    assert res.status == lb.ENOCONV and ref.status == 4
+    assert np.max(rel_eig_err(res.evals, ref.evals)) <= 1e-10
+    s = lb.Solver(**lb.upload_csr(a))
+    with pytest.raises(lb.LobpcgError) as e:
+        s.solve(700, 1e-8)  # 3m > n
+    assert e.value.status == lb.EINVAL
+    with pytest.raises(lb.LobpcgError):
+        s.solve(33, 1e-8)  # m > 32
+    bad = torch.full((2000, 2), float("nan"), dtype=torch.float64, device="cuda")
+    with pytest.raises(lb.LobpcgError) as e:
+        s.solve(2, 1e-8, X0=bad)
+    assert e.value.status == lb.EINVAL
+    s.close()
+    t = lb.upload_csr(a)
+    t["val"][5] = float("inf")
+    with pytest.raises(lb.LobpcgError) as e:
+        lb.Solver(**t)
+    assert e.value.status == lb.EINVAL
+
+
+@pytest.mark.parametrize("dense", [False, True])
+def test_mixed_precision_reaches_fp64_accuracy(dense):
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    if dense:
+        A, d = synth.dense_casscf(n=1024, seed=3, rank=64)
+        k = 4
+        x0 = synth.diag_guess(d, k, seed=3)
+        ref = oracle.lobpcg(A, d, k, x0, tol=1e-8, maxiter=3000)
+        res = _solve(torch, None, k, x0, dense=A, precision=lb.MIXED, maxiter=3000)
+    else:
+        a = synth.sparse_cfg1(n=4096, seed=0)
+        k = 4
+        x0 = synth.diag_guess(a.diag, k, seed=0)
+        ref = oracle.lobpcg(a, a.diag, k, x0, tol=1e-8)
+        res = _solve(torch, a, k, x0, precision=lb.MIXED)
+    assert res.status == 0 and ref.status == 0
+    _parity(res, ref)
+    assert np.max(res.resnorms) <= 1e-8
+    assert res.info["fp64_iterations"] < res.info["iterations"]

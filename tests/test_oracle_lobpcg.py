@@ -105,8 +105,11 @@ def test_cfg1_invariants(cfg1_run):
     gap = np.array([min(abs(w[j] - w[i]) for i in range(6) if i != j) for j in range(4)])
     assert np.all(np.abs(r.evals - w[:4]) <= r.resnorms + 1e-15)
     assert np.all(np.abs(r.evals - w[:4]) <= r.resnorms ** 2 / gap + 1e-14)
-    # soft locking: the active count never grows
-    assert np.all(np.diff(r.hist_mact) <= 0)
+    # soft locking: the locked prefix is exactly the converged prefix of each step
+    for row_res, mact in zip(r.hist_res, r.hist_mact):
+        conv = row_res <= 1e-8
+        prefix = int(np.argmin(conv)) if not conv.all() else len(conv)
+        assert mact == len(conv) - prefix
 
 
 def test_cfg1_paper_statistics(cfg1_run):
@@ -162,3 +165,4 @@ def test_maxiter_reports_noconv_with_best_result():
 def test_invalid_arguments():
     A = np.eye(6)
     assert oracle.lobpcg(A, np.ones(6), 3, np.eye(6)[:, :3].copy(order="F")).status == 1  # 3m > n
+
