@@ -114,6 +114,8 @@ typedef struct {
   double seconds;        /* wall time of the solve on the stream (CUDA events) */
   double phase_seconds[6]; /* with opt.profile: A products, Rayleigh-Ritz Gram, Rayleigh-Ritz
                               eigensolve, basis update + lock, preconditioner, ortho(W; Y) */
+  int64_t kernel_launches; /* CUDA kernels this call launched */
+  int64_t spmm_launches;   /* of which products with A inside the iteration */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */

@@ -48,7 +48,8 @@ class _Info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("fp64_iterations", C.c_int), ("converged", C.c_int),
                 ("cholqr_passes_max", C.c_int), ("ortho_passes_max", C.c_int), ("shifts", C.c_int),
                 ("svqb", C.c_int), ("cap_hits", C.c_int), ("spmm_columns", C.c_int64),
-                ("seconds", C.c_double), ("phase_seconds", C.c_double * 6)]
+                ("seconds", C.c_double), ("phase_seconds", C.c_double * 6), ("kernel_launches", C.c_int64),
+                ("spmm_launches", C.c_int64)]
 
 
 def library_path() -> pathlib.Path:

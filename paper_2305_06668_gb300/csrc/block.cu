@@ -229,18 +229,20 @@ __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __re
                                const double* __restrict__ lam, int c0, int a,
                                const double* __restrict__ diag, int precond, T* __restrict__ W,
                                int ldw) {
-  const int64_t total = n * a;
-  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e / a;
-    const int j = (int)(e - i * a);
-    const double l = lam[c0 + j];
+  // a 2-D walk (row, column) without 64-bit divisions: a warp covers 32 / a rows
+  const int a_pad = a <= 1 ? 1 : (a <= 2 ? 2 : (a <= 4 ? 4 : (a <= 8 ? 8 : (a <= 16 ? 16 : 32))));
+  const int rows_per_block = blockDim.x / a_pad;
+  const int j = threadIdx.x % a_pad;
+  const int rl = threadIdx.x / a_pad;
+  if (j >= a) return;
+  const double l = lam[c0 + j];
+  const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
+  for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rl; i < n; i += (int64_t)gridDim.x * rows_per_block) {
     const T r = AX[i * ld + c0 + j] - (T)l * X[i * ld + c0 + j];
     T w = r;
     if (precond == 1) {
       // computed in the block's precision: FP64 path exact, FP32 path keeps the FP64 units free
       T delta = (T)diag[i] - (T)l;
-      const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
       if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
       w = r / delta;
     }
@@ -360,6 +362,7 @@ int gram_partials(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, dou
                   int max_ctas, cudaStream_t st) {
   const int pa = a.width(), pb = b.width();
   if (pa > kMaxS || pb > kMaxS) throw std::invalid_argument("gram: width > 96");
+  if (const int parts = gram_partials_pipe<T>(n, a, b, upper, part, max_ctas, st)) return parts;
   if (count_tiles(pa, pb, 4, 4, upper) <= 512)
     return gram_launch<T, 4, 4, 32>(n, a, b, upper, part, max_ctas, st);
   return gram_launch<T, 8, 8, 32>(n, a, b, upper, part, max_ctas, st);
@@ -375,6 +378,7 @@ template <class T>
 int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
                   const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
   if (q <= 0 || n <= 0) return 0;
+  if (const int parts = launch_update_pipe<T>(n, job, U, s, q, alpha, lam, norm_part, max_ctas, st)) return parts;
   constexpr int CJ = 4, R = 32;
   const int qpad = round_up(q, CJ);
   const int threads = 256;

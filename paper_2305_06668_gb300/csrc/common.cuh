@@ -25,7 +25,13 @@ struct CudaError : std::runtime_error {
                                 __FILE__ + ":" + std::to_string(__LINE__) + ")");          \
   } while (0)
 
-#define LB_LAUNCH_CHECK() LB_CUDA(cudaGetLastError())
+// Every kernel launch of the library goes through LB_LAUNCH_CHECK, which also counts it.
+long long& launch_counter();
+#define LB_LAUNCH_CHECK()               \
+  do {                                  \
+    ++::lobpcg::launch_counter();       \
+    LB_CUDA(cudaGetLastError());        \
+  } while (0)
 
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 inline int round_up(int a, int b) { return (a + b - 1) / b * b; }
@@ -78,10 +84,15 @@ __device__ __forceinline__ T warp_max(T v) {
 // Launch wrappers (host side).  All take the stream; none synchronises.
 // ----------------------------------------------------------------------------------
 
-// Y = A X, CSR, row-major blocks.  p <= 32.
+// Y = A X, CSR, row-major blocks.  p <= 32.  band >= 0: half-width of the band that holds
+// most non-zeros (from profile_band); the product then stages that window of X in
+// shared memory.
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val,
-                     int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st);
+                     int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band = -1);
+// Smallest half-width b in {16, ..., 2048} with 80% of the non-zeros at |col - row| <= b,
+// or -1 (synchronises the stream).
+int profile_band(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, cudaStream_t st);
 // Y = A X, dense column-major symmetric A.
 template <class T>
 void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, int ldx, T* Y,
@@ -92,6 +103,16 @@ void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, in
 template <class T>
 int gram_partials(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, double* part,
                   int max_ctas, cudaStream_t st);
+// Pipelined variants (tiles.cu) for operands sharing one 16-byte aligned row stride;
+// return 0 without launching when they do not apply.
+template <class T>
+int gram_partials_pipe(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, double* part, int max_ctas,
+                       cudaStream_t st);
+template <class T>
+struct UpdateJob;
+template <class T>
+int launch_update_pipe(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
+                       const double* lam, double* norm_part, int max_ctas, cudaStream_t st);
 // out[e] = sum_g part[g][e] for e < count (FP64, fixed order).
 void reduce_partials(const double* part, int nparts, int count, double* out, cudaStream_t st);
 

@@ -24,6 +24,13 @@
 
 using namespace lobpcg;
 
+namespace lobpcg {
+long long& launch_counter() {
+  static thread_local long long n = 0;
+  return n;
+}
+}  // namespace lobpcg
+
 namespace {
 
 thread_local std::string g_create_error;
@@ -61,6 +68,7 @@ struct NoMem : std::runtime_error {
 struct Stats {
   int cholqr_passes_max = 0, ortho_passes_max = 0, shifts = 0, svqb = 0, cap_hits = 0;
   int64_t spmm_columns = 0;
+  int64_t spmm_launches = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -134,6 +142,7 @@ struct lobpcg_ctx {
   std::string err;
   int sms = 152;
   int max_ctas = 304;
+  int band = -1;  // CSR: half-width holding most non-zeros (shared-memory window of the product)
 
   DevBuf val32, dense32;  // FP32 copies for the mixed form
   Blocks<double> b64;
@@ -203,10 +212,11 @@ void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
   if (p <= 0) return;
   c.prof.mark(PH_SPMM);
   if (c.A.fmt == LOBPCG_CSR)
-    launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st);
+    launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st, c.band);
   else
     launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
   c.stats.spmm_columns += p;
+  c.stats.spmm_launches += 1;
   c.prof.mark(PH_OTHER);
 }
 
@@ -302,6 +312,7 @@ void precondition(lobpcg_ctx& c, const T* X, const T* AX, int ld, int m_conv, in
 }
 
 struct PhaseOut {
+  int sweeps = 0;  // Jacobi sweeps of the last Rayleigh-Ritz solve
   int iterations = 0;
   int m_conv = 0;
   bool converged = false;
@@ -328,7 +339,9 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     LB_CUDA(cudaMemcpyAsync(c.host, c.lock, sizeof(LockState), cudaMemcpyDeviceToHost, c.st));
     LB_CUDA(cudaMemcpyAsync(c.host + 8, c.resnorm, mm * sizeof(double), cudaMemcpyDeviceToHost, c.st));
     LB_CUDA(cudaMemcpyAsync(c.host + 8 + kMaxS, c.lam_all, mm * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    LB_CUDA(cudaMemcpyAsync(c.host + 4, c.ictl + 4, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     c.sync();
+    out.sweeps = *reinterpret_cast<const int*>(c.host + 4);
     std::memcpy(&ls, c.host, sizeof ls);
     out.res.assign(c.host + 8, c.host + 8 + mm);
     out.lam.assign(c.host + 8 + kMaxS, c.host + 8 + kMaxS + mm);
@@ -395,8 +408,8 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     read_lock(m);
     c.prof.mark(PH_OTHER);
     if (c.trace) {
-      std::fprintf(c.trace, "{\"it\": %d, \"prec\": %d, \"s\": %d, \"m_act\": %d, \"lambda\": [", it,
-                   (int)sizeof(T) * 8, s, ls.m_act);
+      std::fprintf(c.trace, "{\"it\": %d, \"prec\": %d, \"s\": %d, \"sweeps\": %d, \"m_act\": %d, \"lambda\": [",
+                   it, (int)sizeof(T) * 8, s, out.sweeps, ls.m_act);
       for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.17g", j ? ", " : "", out.lam[j]);
       std::fprintf(c.trace, "], \"res\": [");
       for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.6e", j ? ", " : "", out.res[j]);
@@ -553,6 +566,7 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
     LB_CUDA(cudaMemcpyAsync(&finite, c->ictl + 5, sizeof(int), cudaMemcpyDeviceToHost, c->st));
     c->sync();
     require(finite == 1, "lobpcg_create: matrix or diagonal has non-finite entries");
+    if (A->fmt == LOBPCG_CSR) c->band = profile_band(A->n, A->row_ptr, A->col_idx, A->nnz, c->st);
     if (c->opt.precision == LOBPCG_MIXED) {
       if (A->fmt == LOBPCG_CSR) {
         c->val32.ensure((size_t)std::max<int64_t>(A->nnz, 1) * sizeof(float));
@@ -586,6 +600,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     require(tol > 0 && std::isfinite(tol), "lobpcg_solve: tol must be positive");
     require(evals && evecs && resnorms, "lobpcg_solve: output pointers must not be NULL");
     c->stats = Stats{};
+    const long long launches0 = launch_counter();
     c->prof.begin(c->opt.profile != 0, c->st);
     const char* tr = std::getenv("LOBPCG_TRACE");
     c->trace = tr && *tr ? std::fopen(tr, "a") : nullptr;
@@ -649,6 +664,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     }
     apply_A<double>(*c, Xs, b.ld, k, AXs, b.ld);
     c->stats.spmm_columns -= k;  // the check product is not part of the iteration
+    c->stats.spmm_launches -= 1;
     {
       // residual norms of the normalised vectors: out = in * I (reuse the update epilogue)
       std::vector<double> eye((size_t)k * k, 0.0);
@@ -690,6 +706,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->spmm_columns = c->stats.spmm_columns;
       info->seconds = ms * 1e-3;
       for (int i = 0; i < 6; ++i) info->phase_seconds[i] = phases[i];
+      info->kernel_launches = launch_counter() - launches0;
+      info->spmm_launches = c->stats.spmm_launches;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))

@@ -1,0 +1,538 @@
+// Pipelined tall-skinny kernels for row-major blocks whose segments share one 16-byte
+// aligned row stride (every block the solver allocates): the Gram / projected
+// matrices C = A^T B of Algorithm 1 and Eq. (CDOrtho), and the basis updates
+// out = base + alpha * in * U (X = V u_x, P = V u_p, W - Y C, W L^{-T}).
+//
+// Each CTA streams its rows in chunks of R rows.  A chunk of every segment is a
+// contiguous R x ld range in global memory, copied with 16-byte cp.async into a
+// multi-stage shared-memory ring (row stride ld + VEC to spread banks), so the loads
+// of chunk k+S-1 overlap the arithmetic on chunk k.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace lobpcg {
+namespace {
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int bytes = valid ? 16 : 0;  // 0 source bytes: the 16 destination bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(bytes));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Issue the copies of rows [r0, r0 + R) of every segment of `c` into dst[seg][R][lds].
+template <class T, int R>
+__device__ __forceinline__ void issue_chunk(const Cols<T>& c, int ld, int lds, int64_t r0, int64_t rend,
+                                            T* dst) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int vpr = ld / VEC;  // 16-byte vectors per row
+  const int total = R * vpr;
+  for (int g = 0; g < c.nseg; ++g) {
+    const T* src = c.p[g];
+    T* d = dst + g * R * lds;
+    for (int i = threadIdx.x; i < total; i += blockDim.x) {
+      const int r = i / vpr, v = i - r * vpr;
+      const int64_t row = r0 + r;
+      const bool ok = row < rend;
+      cp_async16(d + r * lds + v * VEC, src + (ok ? row : 0) * ld + v * VEC, ok);
+    }
+  }
+}
+
+// Padded shared-memory row stride: a multiple of 16 bytes (cp.async destinations) that is
+// an odd multiple of 4 banks, so 8 consecutive rows start in 8 different bank groups.
+template <class T>
+__host__ __device__ __forceinline__ int padded_ld(int ld) {
+  constexpr int VEC = 16 / sizeof(T);
+  int lds = (ld + VEC - 1) / VEC * VEC;
+  while (((lds * (int)sizeof(T) / 4) & 7) != 4) lds += VEC;
+  return lds;
+}
+
+// Shared-memory offset (within one stage) of logical column `col` of `c`, or -1.
+template <class T>
+__device__ __forceinline__ int col_offset(const Cols<T>& c, int col, int R, int lds) {
+  int base = 0;
+  for (int g = 0; g < c.nseg; ++g) {
+    if (col < base + c.w[g]) return g * R * lds + (col - base);
+    base += c.w[g];
+  }
+  return -1;
+}
+
+// ------------------------------------------------------------------------ Gram
+template <class T, int TI, int TJ, int R, int S>
+__global__ void __launch_bounds__(256) gram_pipe_kernel(int64_t n, Cols<T> A, Cols<T> B, int ld, int upper,
+                                                        int ntiles, int groups, double* __restrict__ part,
+                                                        int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lds = padded_ld<T>(ld);
+  const int stageA = A.nseg * R * lds, stageB = B.nseg * R * lds;
+  const int stage = stageA + stageB;
+  T* ring = reinterpret_cast<T*>(smem_raw);
+  __shared__ short tile_i[kMaxS * kMaxS / 16], tile_j[kMaxS * kMaxS / 16];
+  const int pa = A.width(), pb = B.width();
+  const int nti = (pa + TI - 1) / TI, ntj = (pb + TJ - 1) / TJ;
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    for (int tj = 0; tj < ntj; ++tj)
+      for (int ti = 0; ti < nti; ++ti)
+        if (!upper || ti * TI <= tj * TJ + TJ - 1) tile_i[idx] = (short)ti, tile_j[idx] = (short)tj, ++idx;
+  }
+  __syncthreads();
+  const int t = threadIdx.x % ntiles, grp = threadIdx.x / ntiles;
+  const bool active = grp < groups;
+  int offA[TI], offB[TJ];
+#pragma unroll
+  for (int i = 0; i < TI; ++i) offA[i] = col_offset(A, tile_i[t] * TI + i, R, lds);
+#pragma unroll
+  for (int j = 0; j < TJ; ++j) offB[j] = col_offset(B, tile_j[t] * TJ + j, R, lds);
+
+  T acc[TI][TJ];
+#pragma unroll
+  for (int i = 0; i < TI; ++i)
+#pragma unroll
+    for (int j = 0; j < TJ; ++j) acc[i][j] = T(0);
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  const int nchunks = (int)((r_end - r_begin + R - 1) / R);
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if (k < nchunks) {
+      issue_chunk<T, R>(A, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage);
+      issue_chunk<T, R>(B, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage + stageA);
+    }
+    cp_async_commit();
+  }
+  for (int k = 0; k < nchunks; ++k) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    {
+      const int kn = k + S - 1;
+      if (kn < nchunks) {
+        T* dst = ring + (kn % S) * stage;
+        issue_chunk<T, R>(A, ld, lds, r_begin + (int64_t)kn * R, r_end, dst);
+        issue_chunk<T, R>(B, ld, lds, r_begin + (int64_t)kn * R, r_end, dst + stageA);
+      }
+      cp_async_commit();
+    }
+    if (active) {
+      const T* sa = ring + (k % S) * stage;
+      const T* sb = sa + stageA;
+      for (int r = grp; r < R; r += groups) {
+        T a[TI], b[TJ];
+#pragma unroll
+        for (int i = 0; i < TI; ++i) a[i] = offA[i] >= 0 ? sa[offA[i] + r * lds] : T(0);
+#pragma unroll
+        for (int j = 0; j < TJ; ++j) b[j] = offB[j] >= 0 ? sb[offB[j] + r * lds] : T(0);
+#pragma unroll
+        for (int i = 0; i < TI; ++i)
+#pragma unroll
+          for (int j = 0; j < TJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // groups add their sums into shared memory one after another (fixed order)
+  double* scratch = reinterpret_cast<double*>(smem_raw);
+  constexpr int per = TI * TJ;
+  for (int g = 0; g < groups; ++g) {
+    if (active && grp == g) {
+#pragma unroll
+      for (int i = 0; i < TI; ++i)
+#pragma unroll
+        for (int j = 0; j < TJ; ++j) {
+          double& dst = scratch[t * per + i * TJ + j];
+          dst = (g == 0 ? 0.0 : dst) + (double)acc[i][j];
+        }
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.x * pa * pb;
+  for (int e = threadIdx.x; e < ntiles * per; e += blockDim.x) {
+    const int tt = e / per, ij = e % per;
+    const int i = tile_i[tt] * TI + ij / TJ, j = tile_j[tt] * TJ + ij % TJ;
+    if (i < pa && j < pb && (!upper || i <= j)) out[i + j * pa] = scratch[e];
+  }
+}
+
+// ------------------------------------------------------------------------ update
+// Thread (rg, cg) computes RJ rows x CJ columns of every product of the job.
+template <class T, int RJ, int CJ, int R, int S>
+__global__ void __launch_bounds__(256) update_pipe_kernel(int64_t n, UpdateJob<T> job, int ld,
+                                                          const double* __restrict__ U, int s, int q,
+                                                          double alpha, const double* __restrict__ lam,
+                                                          double* __restrict__ norm_part, int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lds = padded_ld<T>(ld);
+  const int qpad = (q + CJ - 1) / CJ * CJ;
+  T* sU = reinterpret_cast<T*>(smem_raw);                        // s x qpad
+  int* offs = reinterpret_cast<int*>(sU + ((s * qpad + 3) / 4) * 4);  // s column offsets
+  T* ring = reinterpret_cast<T*>(offs + ((s + 3) / 4) * 4);
+  const int stage_in = job.in[0].nseg * R * lds;
+  const int stage = job.nprod * stage_in;
+  for (int e = threadIdx.x; e < s * qpad; e += blockDim.x) {
+    const int l = e / qpad, j = e % qpad;
+    sU[e] = j < q ? (T)U[l + j * s] : T(0);
+  }
+  for (int l = threadIdx.x; l < s; l += blockDim.x) offs[l] = col_offset(job.in[0], l, R, lds);
+  const int cgs = qpad / CJ, rgs = R / RJ;
+  const int cg = threadIdx.x % cgs, rg = threadIdx.x / cgs;
+  const bool active = rg < rgs;
+  double nsum[CJ], nmax[CJ];
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) nsum[j] = 0.0, nmax[j] = 0.0;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  const int nchunks = (int)((r_end - r_begin + R - 1) / R);
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if (k < nchunks)
+      for (int t = 0; t < job.nprod; ++t)
+        issue_chunk<T, R>(job.in[t], ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage + t * stage_in);
+    cp_async_commit();
+  }
+  for (int k = 0; k < nchunks; ++k) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    {
+      const int kn = k + S - 1;
+      if (kn < nchunks)
+        for (int t = 0; t < job.nprod; ++t)
+          issue_chunk<T, R>(job.in[t], ld, lds, r_begin + (int64_t)kn * R, r_end,
+                            ring + (kn % S) * stage + t * stage_in);
+      cp_async_commit();
+    }
+    if (!active) continue;
+    const int64_t row0 = r_begin + (int64_t)k * R + rg;  // rows row0 + r * rgs, r < RJ
+    T res[2][RJ][CJ];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= job.nprod) break;
+      const T* sin = ring + (k % S) * stage + t * stage_in + rg * lds;
+      T acc[RJ][CJ];
+#pragma unroll
+      for (int r = 0; r < RJ; ++r)
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) acc[r][j] = T(0);
+      for (int l = 0; l < s; ++l) {
+        const int o = offs[l];
+        T u[CJ];
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) u[j] = sU[l * qpad + cg * CJ + j];
+#pragma unroll
+        for (int r = 0; r < RJ; ++r) {
+          const T x = sin[o + r * rgs * lds];
+#pragma unroll
+          for (int j = 0; j < CJ; ++j) acc[r][j] = fma(x, u[j], acc[r][j]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RJ; ++r) {
+        const int64_t row = row0 + (int64_t)r * rgs;
+        if (row >= r_end) continue;
+        T* o = job.out[t] + row * job.ld_out[t];
+        const T* b = job.base[t] ? job.base[t] + row * job.ld_base[t] : nullptr;
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          const int col = cg * CJ + j;
+          T v = (T)alpha * acc[r][j];
+          if (b && col < q) v = b[col] + v;
+          res[t][r][j] = v;
+          if (col < q) o[col] = v;
+        }
+      }
+    }
+    if (norm_part) {
+#pragma unroll
+      for (int r = 0; r < RJ; ++r) {
+        if (row0 + (int64_t)r * rgs >= r_end) continue;
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          const int col = cg * CJ + j;
+          if (col < q) {
+            const T rij = res[1][r][j] - (T)lam[col] * res[0][r][j];
+            nsum[j] += (double)(rij * rij);
+            nmax[j] = fmax(nmax[j], (double)fabs(rij));
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!norm_part) return;
+  __syncthreads();
+  double* sN = reinterpret_cast<double*>(ring);  // [rgs][2 * qpad]
+  if (active)
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      sN[rg * 2 * qpad + cg * CJ + j] = nsum[j];
+      sN[rg * 2 * qpad + qpad + cg * CJ + j] = nmax[j];
+    }
+  __syncthreads();
+  for (int col = threadIdx.x; col < q; col += blockDim.x) {
+    double s2 = 0.0, mx = 0.0;
+    for (int g = 0; g < rgs; ++g) {
+      s2 += sN[g * 2 * qpad + col];
+      mx = fmax(mx, sN[g * 2 * qpad + qpad + col]);
+    }
+    norm_part[(int64_t)blockIdx.x * 2 * q + col] = s2;
+    norm_part[(int64_t)blockIdx.x * 2 * q + q + col] = mx;
+  }
+}
+
+
+// ------------------------------------------------------------------------ update, one row per thread
+// out_t = base_t + alpha * in_t * U with U (s x q, q <= QMAX) broadcast from shared memory
+// and each thread streaming its own input row with 16-byte loads (the row's lines stay
+// in L1 while the thread walks them).  Used for every update of the solver.
+template <class T>
+struct V16;
+template <>
+struct V16<float> {
+  using type = float4;
+};
+template <>
+struct V16<double> {
+  using type = double2;
+};
+
+template <class T, int QMAX>
+__global__ void __launch_bounds__(256) update_row_kernel(int64_t n, UpdateJob<T> job, int ld,
+                                                         const double* __restrict__ U, int s, int q,
+                                                         double alpha, const double* __restrict__ lam,
+                                                         double* __restrict__ norm_part, int64_t rows_per_cta) {
+  using VT = typename V16<T>::type;
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int QV = QMAX / VEC;  // vectors per U row
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  VT* sU = reinterpret_cast<VT*>(smem_raw);  // s rows of QV vectors
+  for (int e = threadIdx.x; e < s * QMAX; e += blockDim.x) {
+    const int l = e / QMAX, j = e % QMAX;
+    reinterpret_cast<T*>(sU)[e] = j < q ? (T)U[l + j * s] : T(0);
+  }
+  __syncthreads();
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  T nsum[QMAX], nmax[QMAX];  // per-thread partial column sums of r^2 and max |r|
+  if (norm_part)
+#pragma unroll
+    for (int j = 0; j < QMAX; ++j) nsum[j] = T(0), nmax[j] = T(0);
+  for (int64_t row = r_begin + threadIdx.x; row < r_end; row += blockDim.x) {
+    T res[2][QMAX];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= job.nprod) break;
+      const Cols<T>& in = job.in[t];
+#pragma unroll
+      for (int j = 0; j < QMAX; ++j) res[t][j] = T(0);
+      int l0 = 0;
+      for (int g = 0; g < in.nseg; ++g) {
+        const T* xr = in.p[g] + row * ld;
+        const int w = in.w[g];
+        for (int c = 0; c < w; c += VEC) {
+          const VT xv = *reinterpret_cast<const VT*>(xr + c);
+          const T* xs = reinterpret_cast<const T*>(&xv);
+#pragma unroll
+          for (int i = 0; i < VEC; ++i) {
+            if (c + i >= w) break;
+            const T x = xs[i];
+            const VT* ur = sU + (l0 + c + i) * QV;
+#pragma unroll
+            for (int jv = 0; jv < QV; ++jv) {
+              const VT u = ur[jv];
+              const T* us = reinterpret_cast<const T*>(&u);
+#pragma unroll
+              for (int k = 0; k < VEC; ++k) res[t][jv * VEC + k] = fma(x, us[k], res[t][jv * VEC + k]);
+            }
+          }
+        }
+        l0 += w;
+      }
+      T* o = job.out[t] + row * job.ld_out[t];
+      const T* b = job.base[t] ? job.base[t] + row * job.ld_base[t] : nullptr;
+#pragma unroll
+      for (int j = 0; j < QMAX; ++j) {
+        if (j < q) {
+          T v = (T)alpha * res[t][j];
+          if (b) v = b[j] + v;
+          res[t][j] = v;
+          o[j] = v;
+        }
+      }
+    }
+    if (norm_part) {
+#pragma unroll
+      for (int j = 0; j < QMAX; ++j) {
+        if (j < q) {
+          const T rij = res[1][j] - (T)lam[j] * res[0][j];
+          nsum[j] = fma(rij, rij, nsum[j]);
+          nmax[j] = fmax(nmax[j], fabs(rij));
+        }
+      }
+    }
+  }
+  if (!norm_part) return;
+  // CTA reduction of the per-column partial norms: warp shuffles, then warps in order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(smem_raw);  // [warps][2 * QMAX]
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int j = 0; j < QMAX; ++j) {
+    if (j >= q) break;
+    const double a = warp_sum((double)nsum[j]);
+    const double m = warp_max((double)nmax[j]);
+    if (lane == 0) red[wid * 2 * QMAX + j] = a, red[wid * 2 * QMAX + QMAX + j] = m;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double a = 0.0, m = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) a += red[w2 * 2 * QMAX + j], m = fmax(m, red[w2 * 2 * QMAX + QMAX + j]);
+    norm_part[(int64_t)blockIdx.x * 2 * q + j] = a;
+    norm_part[(int64_t)blockIdx.x * 2 * q + q + j] = m;
+  }
+}
+
+template <class T, int QMAX>
+int update_row_launch(int64_t n, const UpdateJob<T>& job, int ld, const double* U, int s, int q, double alpha,
+                      const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  const int threads = 256;
+  const size_t smem = std::max((size_t)s * QMAX * sizeof(T), (size_t)(threads / 32) * 2 * QMAX * sizeof(double));
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(update_row_kernel<T, QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 64 * 1024));
+    attr = true;
+  }
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, threads));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = ceil_div(n, ctas);
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  update_row_kernel<T, QMAX><<<(unsigned)ctas, threads, smem, st>>>(n, job, ld, U, s, q, alpha, lam, norm_part, rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
+int count_tiles(int pa, int pb, int TI, int TJ, bool upper) {
+  const int nti = (pa + TI - 1) / TI, ntj = (pb + TJ - 1) / TJ;
+  int ntiles = 0;
+  for (int tj = 0; tj < ntj; ++tj)
+    for (int ti = 0; ti < nti; ++ti)
+      if (!upper || ti * TI <= tj * TJ + TJ - 1) ++ntiles;
+  return ntiles;
+}
+
+template <class T>
+bool aligned(const Cols<T>& c, int ld) {
+  for (int g = 0; g < c.nseg; ++g)
+    if (c.ld[g] != ld || (reinterpret_cast<uintptr_t>(c.p[g]) & 15)) return false;
+  return (ld * sizeof(T)) % 16 == 0;
+}
+
+template <class T, int TI, int TJ, int R, int S>
+int gram_pipe_launch(int64_t n, const Cols<T>& a, const Cols<T>& b, int ld, bool upper, double* part,
+                     int max_ctas, cudaStream_t st) {
+  const int pa = a.width(), pb = b.width();
+  const int ntiles = count_tiles(pa, pb, TI, TJ, upper);
+  const int threads = 256;
+  const int groups = std::max(1, threads / ntiles);
+  const int lds = padded_ld<T>(ld);
+  const size_t ring = (size_t)S * (a.nseg + b.nseg) * R * lds * sizeof(T);
+  const size_t red = (size_t)ntiles * TI * TJ * sizeof(double);
+  const size_t smem = std::max(ring, red);
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(gram_pipe_kernel<T, TI, TJ, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr = true;
+  }
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  gram_pipe_kernel<T, TI, TJ, R, S><<<(unsigned)ctas, threads, smem, st>>>(n, a, b, ld, upper ? 1 : 0, ntiles,
+                                                                          groups, part, rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
+}  // namespace
+
+// Pipelined Gram partials; returns 0 (nothing launched) when the operands do not share
+// one aligned row stride, so the caller can use the general kernel instead.
+template <class T>
+int gram_partials_pipe(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, double* part, int max_ctas,
+                       cudaStream_t st) {
+  if (a.nseg == 0 || b.nseg == 0) return 0;
+  const int ld = a.ld[0];
+  if (!aligned(a, ld) || !aligned(b, ld)) return 0;
+  const int pa = a.width(), pb = b.width();
+  const size_t ring_per_stage = (size_t)(a.nseg + b.nseg) * 32 * padded_ld<T>(ld) * sizeof(T);
+  if (ring_per_stage * 2 > 190 * 1024) return 0;
+  if (sizeof(T) == 4 && pa >= 16 && pb >= 16 && count_tiles(pa, pb, 8, 8, upper) <= 256) {
+    // long stages: enough rows per thread group between barriers
+    const size_t stage128 = (size_t)(a.nseg + b.nseg) * 128 * padded_ld<T>(ld) * sizeof(T);
+    if (stage128 * 2 <= 190 * 1024) return gram_pipe_launch<T, 8, 8, 128, 2>(n, a, b, ld, upper, part, max_ctas, st);
+    return gram_pipe_launch<T, 8, 8, 32, 3>(n, a, b, ld, upper, part, max_ctas, st);
+  }
+  if (count_tiles(pa, pb, 4, 4, upper) <= 256)
+    return gram_pipe_launch<T, 4, 4, 32, 2>(n, a, b, ld, upper, part, max_ctas, st);
+  return 0;
+}
+
+template <class T>
+int launch_update_pipe(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
+                       const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  if (job.in[0].nseg == 0) return 0;
+  // FP64 updates are bound by the FP64 units, where the general kernel does as well
+  if (sizeof(T) == 8) return 0;
+  const int ld = job.in[0].ld[0];
+  for (int t = 0; t < job.nprod; ++t)
+    if (!aligned(job.in[t], ld) || job.in[t].nseg != job.in[0].nseg) return 0;
+  if (q <= 8) return update_row_launch<T, 8>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  if (q <= 16) return update_row_launch<T, 16>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  if (q <= 24) return update_row_launch<T, 24>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  if (q <= 32) return update_row_launch<T, 32>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  constexpr int RJ = 4, CJ = 4, R = 64, S = 2;
+  const int lds = padded_ld<T>(ld);
+  const int qpad = round_up(q, CJ);
+  if (qpad / CJ * (R / RJ) > 256) return 0;
+  const size_t head = (size_t)((s * qpad + 3) / 4 * 4) * sizeof(T) + (size_t)((s + 3) / 4 * 4) * sizeof(int);
+  const size_t ring = (size_t)S * job.nprod * job.in[0].nseg * R * lds * sizeof(T);
+  const size_t red = norm_part ? (size_t)(R / RJ) * 2 * qpad * sizeof(double) : 0;
+  const size_t smem = head + std::max(ring, red) + 16;
+  if (smem > 200 * 1024) return 0;
+  static bool attr = false;
+  if (!attr) {
+    LB_CUDA(cudaFuncSetAttribute(update_pipe_kernel<T, RJ, CJ, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    attr = true;
+  }
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  update_pipe_kernel<T, RJ, CJ, R, S><<<(unsigned)ctas, 256, smem, st>>>(n, job, ld, U, s, q, alpha, lam, norm_part,
+                                                                        rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
+template int gram_partials_pipe<double>(int64_t, const Cols<double>&, const Cols<double>&, bool, double*, int,
+                                        cudaStream_t);
+template int gram_partials_pipe<float>(int64_t, const Cols<float>&, const Cols<float>&, bool, double*, int,
+                                       cudaStream_t);
+template int launch_update_pipe<double>(int64_t, const UpdateJob<double>&, const double*, int, int, double,
+                                        const double*, double*, int, cudaStream_t);
+template int launch_update_pipe<float>(int64_t, const UpdateJob<float>&, const double*, int, int, double,
+                                       const double*, double*, int, cudaStream_t);
+
+}  // namespace lobpcg
