@@ -192,6 +192,25 @@ LOBPCG_API lobpcg_status lobpcg_ortho_against_f64(int64_t n, int p, double* X, i
                                        const double* Y, int ldy, double tau, int cap, int cap2,
                                        int* stats, lobpcg_stream stream);
 
+/* C = X^T Y exactly like lobpcg_gram_f64, but without allocating any memory.  The paper
+ * has no counterpart; this entry point exists for callers that cannot allocate device
+ * memory: for example a serving loop that sizes all of its GPU memory at start-up and
+ * must not call cudaMalloc afterwards (cudaMalloc can synchronise the device and can
+ * fail under memory pressure), or code whose device memory is owned by another
+ * allocator.  The split-row partial sums go to a fixed array in the library,
+ * 152 x 1024 doubles (1.2 MB), which every GPU that loads the library holds until the
+ * process exits.
+ *   n >= 1; 1 <= p, q; p * q <= 1024 (else LOBPCG_EINVAL); X: n x p (ldx), Y: n x q (ldy),
+ *   row-major, device; C: device, column-major p x q.
+ * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
+ * with the device current; make that first call before any stream capture.  All calls
+ * share the one array: calls whose work overlaps on the GPU (different streams or
+ * threads) race and give wrong results; serialise them.  Every partial sum a call
+ * reads is written by that same call, so nothing left by an earlier call leaks into
+ * the result.  Returns after the stream has finished the work. */
+LOBPCG_API lobpcg_status lobpcg_gram_f64_noalloc(int64_t n, int p, const double* X, int ldx, int q,
+                                                 const double* Y, int ldy, double* C, lobpcg_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,7 +65,7 @@ def lib():
         L = C.CDLL(str(_LIB_PATH))
         for name in ("lobpcg_options_default", "lobpcg_create", "lobpcg_solve", "lobpcg_spmm_csr_f64",
                      "lobpcg_spmm_dense_f64", "lobpcg_gram_f64", "lobpcg_syev_f64", "lobpcg_ortho_f64",
-                     "lobpcg_ortho_against_f64"):
+                     "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -229,6 +229,21 @@ def gram(X, Y, stream=None):
     Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)  # column-major p x q
     _check(lib().lobpcg_gram_f64(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
                                  C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
+    return Cm.t()
+
+
+def gram_noalloc(X, Y, out=None, stream=None):
+    """C = X^T Y through the entry point that allocates no device memory itself.
+
+    ``out`` may be a preallocated (q, p) float64 CUDA tensor (column-major storage of the
+    p x q result); its transpose is returned.
+    """
+    torch = _torch()
+    n, p = X.shape
+    q = Y.shape[1]
+    Cm = torch.empty((q, p), dtype=torch.float64, device=X.device) if out is None else out
+    _check(lib().lobpcg_gram_f64_noalloc(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q),
+                                         _ptr(Y), C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
     return Cm.t()
 
 

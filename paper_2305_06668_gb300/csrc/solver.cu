@@ -24,16 +24,22 @@
 
 using namespace lobpcg;
 
+namespace {
+thread_local std::string g_create_error;
+}
+
 namespace lobpcg {
 long long& launch_counter() {
   static thread_local long long n = 0;
   return n;
 }
+const char* set_thread_error(const std::string& msg) {
+  g_create_error = msg;
+  return g_create_error.c_str();
+}
 }  // namespace lobpcg
 
 namespace {
-
-thread_local std::string g_create_error;
 
 struct DevBuf {
   void* p = nullptr;
