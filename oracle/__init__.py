@@ -185,3 +185,41 @@ def lobpcg(A, diag, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, m
 
 def threads() -> int:
     return lib().oracle_threads()
+
+
+# ------------------------------------------------------------------ learned preconditioner scale
+
+def mlp_num_params() -> int:
+    lib().oracle_mlp_num_params.restype = C.c_int
+    return lib().oracle_mlp_num_params()
+
+
+def mlp_forward(P: np.ndarray, F: np.ndarray) -> np.ndarray:
+    """s = softplus(MLP(f)) for features F (N x 3) and parameters P (float64)."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    s = np.zeros(F.shape[0])
+    lib().oracle_mlp_forward(_p(P), C.c_int64(F.shape[0]), _p(F), _p(s))
+    return s
+
+
+def mlp_backward(P: np.ndarray, F: np.ndarray, g: np.ndarray) -> np.ndarray:
+    """sum_i g_i ds_i/dP."""
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    grad = np.zeros_like(P)
+    lib().oracle_mlp_backward(_p(P), C.c_int64(F.shape[0]), _p(F), _p(g), _p(grad))
+    return grad
+
+
+def mlp_loss(col, q, e, s, far_we, far_ww, ee):
+    """Mean over columns of 1 - cos^2(w, e) with w = s q; returns (loss, dL/ds)."""
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    q, e, s = (np.ascontiguousarray(v, dtype=np.float64) for v in (q, e, s))
+    far_we, far_ww, ee = (np.ascontiguousarray(v, dtype=np.float64) for v in (far_we, far_ww, ee))
+    d = np.zeros_like(s)
+    lib().oracle_mlp_loss.restype = C.c_double
+    loss = lib().oracle_mlp_loss(C.c_int64(len(s)), C.c_int(len(ee)), _p(col), _p(q), _p(e), _p(s), _p(far_we),
+                                 _p(far_ww), _p(ee), _p(d))
+    return loss, d
