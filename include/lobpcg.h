@@ -95,7 +95,8 @@ typedef struct {
   int ortho_cap;              /* Cholesky-QR passes per ortho(X), default 6 */
   int ortho2_cap;             /* projection passes per ortho(X, Y), default 4 */
   uint64_t seed;              /* seed of the random initial block when X0 == NULL */
-  const float* mlp_weights;   /* host, learned preconditioner weights (LOBPCG_PREC_LEARNED), see lobpcg_mlp_num_weights */
+  const float* mlp_weights;   /* host, lobpcg_mlp_num_params() learned-preconditioner parameters
+                                 (LOBPCG_PREC_LEARNED); copied by lobpcg_create */
   int profile;                /* non-zero: fill lobpcg_info.phase_seconds (adds CUDA events) */
   double mixed_switch;        /* MIXED: leave FP32 once the k sought residuals are <= this;
                                  0 (default) = when the largest stops improving */
@@ -116,6 +117,7 @@ typedef struct {
                               eigensolve, basis update + lock, preconditioner, ortho(W; Y) */
   int64_t kernel_launches; /* CUDA kernels this call launched */
   int64_t spmm_launches;   /* of which products with A inside the iteration */
+  int precond_fallback;    /* 1 if the learned preconditioner stalled and the diagonal one took over */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
@@ -191,6 +193,63 @@ LOBPCG_API lobpcg_status lobpcg_ortho_f64(int64_t n, int p, double* X, int ldx, 
 LOBPCG_API lobpcg_status lobpcg_ortho_against_f64(int64_t n, int p, double* X, int ldx, int q,
                                        const double* Y, int ldy, double tau, int cap, int cap2,
                                        int* stats, lobpcg_stream stream);
+
+/* ------------------------------------------------------------------------------
+ * Learned preconditioner (LOBPCG_PREC_LEARNED).  Not in the paper; its preconditioner
+ * study (Sec. 4.4, Table 1) motivates correcting the diagonal step of Sec. 2.  Per
+ * (row i, active column j) a 3 -> 64 -> 64 -> 1 ReLU perceptron gives z and
+ *     w_ij = softplus(z) r_ij / (d_i - theta_j)
+ * for rows with |d_i - theta_j| <= 64 c (c = mean off-diagonal row 2-norm rho); other
+ * rows keep the diagonal step.  Features: f1 = (d_i - theta_j) / (8 c), f2 = rho_i / c,
+ * f3 = r_ij / max_i |r_ij|.  Weights and activations are BF16, sums FP32.  Parameter
+ * vector (float, lobpcg_mlp_num_params() = 4481 entries, row-major out x in):
+ *     W1[64][3] b1[64] W2[64][64] b2[64] W3[64] b3[1].
+ * The entry points below train it; all arrays are device arrays and every call returns
+ * after the stream has finished its work.
+ * ------------------------------------------------------------------------------ */
+
+/* Number of parameters of the perceptron (4481). */
+LOBPCG_API int lobpcg_mlp_num_params(void);
+
+/* s_i = softplus(MLP(F_i)) for N samples; F: N x 3 row-major.  bf16 != 0 rounds
+ * weights, inputs and activations to BF16 as the solver does; bf16 == 0 keeps FP32
+ * (only for checking the arithmetic). */
+LOBPCG_API lobpcg_status lobpcg_mlp_forward(int64_t N, const float* F, const float* params, float* s, int bf16,
+                                            lobpcg_stream stream);
+
+/* grad += sum_i g_i ds_i / dparams, taken at the (BF16-rounded when bf16 != 0) parameters. */
+LOBPCG_API lobpcg_status lobpcg_mlp_backward(int64_t N, const float* F, const float* params, const float* g,
+                                             float* grad, int bf16, lobpcg_stream stream);
+
+/* Training loss: samples grouped by column col[i] in [0, ncol); w_i = s_i q_i;
+ * per column L_c = 1 - (w.e)^2 / (|w|^2 ee_c) with the fixed contributions far_we_c,
+ * far_ww_c of the rows outside the learned region added to w.e and |w|^2.
+ *   work: device, 2 ncol doubles;  loss: device double, mean of L_c;  dLds: dloss/ds_i. */
+LOBPCG_API lobpcg_status lobpcg_mlp_loss(int64_t N, int ncol, const int32_t* col, const float* q, const float* e,
+                                         const float* s, const double* far_we, const double* far_ww, const double* ee,
+                                         double* work, float* dLds, double* loss, lobpcg_stream stream);
+
+/* One Adam step on params (FP32 master copy) from grad, which is then zeroed.
+ * np must equal lobpcg_mlp_num_params(); step >= 1 is the 1-based step count. */
+LOBPCG_API lobpcg_status lobpcg_mlp_adam(int np, float* params, float* grad, float* m, float* v, int step, float lr,
+                                         float beta1, float beta2, float eps, lobpcg_stream stream);
+
+/* Training features of a block of Ritz pairs (row-major X, AX: n x p, ld): for every
+ * (row i, column j): F (3 floats, as above), q = r_ij / guard(d_i - lam_j), e = XS_ij -
+ * alpha_j X_ij (the exact correction made orthogonal to x_j when XS holds the aligned
+ * exact eigenvector and alpha_j = x_j . XS_j), near flag; and per column (sums, 3 p
+ * doubles): |e|^2 over all rows, then (q e) and q^2 summed over the rows outside the
+ * learned region.  rho / cscale: from lobpcg_row_norms; colmax_j = max_i |r_ij|. */
+LOBPCG_API lobpcg_status lobpcg_precond_features(int64_t n, int p, const double* X, const double* AX, int ld,
+                                                 const double* lam, const double* diag, const float* rho, float cscale,
+                                                 const double* colmax, const double* XS, const double* alpha, float* F,
+                                                 float* q, float* e, int* near, double* sums, lobpcg_stream stream);
+
+/* rho_i = off-diagonal 2-norm of row i of A (CSR, or dense column-major when dense != NULL);
+ * *mean_out (host) = mean of rho. */
+LOBPCG_API lobpcg_status lobpcg_row_norms(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                          const double* val, const double* dense, int64_t lda, float* rho,
+                                          double* mean_out, lobpcg_stream stream);
 
 /* C = X^T Y exactly like lobpcg_gram_f64, but without allocating any memory.  The paper
  * has no counterpart; this entry point exists for callers that cannot allocate device

@@ -49,7 +49,7 @@ class _Info(C.Structure):
                 ("cholqr_passes_max", C.c_int), ("ortho_passes_max", C.c_int), ("shifts", C.c_int),
                 ("svqb", C.c_int), ("cap_hits", C.c_int), ("spmm_columns", C.c_int64),
                 ("seconds", C.c_double), ("phase_seconds", C.c_double * 6), ("kernel_launches", C.c_int64),
-                ("spmm_launches", C.c_int64)]
+                ("spmm_launches", C.c_int64), ("precond_fallback", C.c_int)]
 
 
 def library_path() -> pathlib.Path:
@@ -65,7 +65,9 @@ def lib():
         L = C.CDLL(str(_LIB_PATH))
         for name in ("lobpcg_options_default", "lobpcg_create", "lobpcg_solve", "lobpcg_spmm_csr_f64",
                      "lobpcg_spmm_dense_f64", "lobpcg_gram_f64", "lobpcg_syev_f64", "lobpcg_ortho_f64",
-                     "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc"):
+                     "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
+                     "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
+                     "lobpcg_row_norms", "lobpcg_mlp_num_params"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -284,3 +286,78 @@ def upload_csr(a, device="cuda"):
                 col_idx=torch.from_numpy(np.ascontiguousarray(a.col_idx, dtype=np.int32)).to(device),
                 val=torch.from_numpy(np.ascontiguousarray(a.val, dtype=np.float64)).to(device),
                 diag=torch.from_numpy(np.ascontiguousarray(a.diag, dtype=np.float64)).to(device))
+
+
+# ------------------------------------------------------------------ learned preconditioner
+
+def mlp_num_params() -> int:
+    return lib().lobpcg_mlp_num_params()
+
+
+def mlp_forward(F, params, bf16=True, stream=None):
+    """s = softplus(MLP(F)) for features F (N x 3 float32 CUDA) and float32 parameters."""
+    torch = _torch()
+    s = torch.empty(F.shape[0], dtype=torch.float32, device=F.device)
+    _check(lib().lobpcg_mlp_forward(C.c_int64(F.shape[0]), _ptr(F), _ptr(params), _ptr(s), C.c_int(int(bf16)),
+                                    _stream(stream)))
+    return s
+
+
+def mlp_backward(F, params, g, grad, bf16=True, stream=None):
+    """grad += sum_i g_i ds_i/dparams (in place)."""
+    _check(lib().lobpcg_mlp_backward(C.c_int64(F.shape[0]), _ptr(F), _ptr(params), _ptr(g), _ptr(grad),
+                                     C.c_int(int(bf16)), _stream(stream)))
+    return grad
+
+
+def mlp_loss(col, q, e, s, far_we, far_ww, ee, stream=None):
+    """Returns (mean column loss as a float, dL/ds CUDA tensor)."""
+    torch = _torch()
+    ncol = ee.numel()
+    work = torch.empty(2 * ncol, dtype=torch.float64, device=q.device)
+    loss = torch.empty(1, dtype=torch.float64, device=q.device)
+    d = torch.empty_like(s)
+    _check(lib().lobpcg_mlp_loss(C.c_int64(s.numel()), C.c_int(ncol), _ptr(col), _ptr(q), _ptr(e), _ptr(s),
+                                 _ptr(far_we), _ptr(far_ww), _ptr(ee), _ptr(work), _ptr(d), _ptr(loss),
+                                 _stream(stream)))
+    return float(loss.item()), d
+
+
+def mlp_adam(params, grad, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().lobpcg_mlp_adam(C.c_int(params.numel()), _ptr(params), _ptr(grad), _ptr(m), _ptr(v), C.c_int(step),
+                                 C.c_float(lr), C.c_float(beta1), C.c_float(beta2), C.c_float(eps), _stream(stream)))
+
+
+def row_norms(diag_n, row_ptr=None, col_idx=None, val=None, dense=None, stream=None):
+    """(rho, mean rho): off-diagonal 2-norms of the rows of A."""
+    torch = _torch()
+    n = diag_n
+    rho = torch.empty(n, dtype=torch.float32, device="cuda")
+    mean = C.c_double(0.0)
+    At = None if dense is None else (dense if dense.t().is_contiguous() else dense.t().contiguous().t())
+    _check(lib().lobpcg_row_norms(C.c_int64(n), _ptr(row_ptr), _ptr(col_idx), _ptr(val), _ptr(At), C.c_int64(n),
+                                  _ptr(rho), C.byref(mean), _stream(stream)))
+    return rho, mean.value
+
+
+def precond_features(X, AX, lam, diag, rho, cscale, colmax, XS, alpha, stream=None):
+    """Training features of a row-major block (see lobpcg_precond_features)."""
+    torch = _torch()
+    n, p = X.shape
+    dev = X.device
+    F = torch.empty((n * p, 3), dtype=torch.float32, device=dev)
+    q = torch.empty(n * p, dtype=torch.float32, device=dev)
+    e = torch.empty(n * p, dtype=torch.float32, device=dev)
+    near = torch.empty(n * p, dtype=torch.int32, device=dev)
+    sums = torch.empty(3 * p, dtype=torch.float64, device=dev)
+    _check(lib().lobpcg_precond_features(C.c_int64(n), C.c_int(p), _ptr(X), _ptr(AX), C.c_int(X.stride(0)),
+                                         _ptr(lam), _ptr(diag), _ptr(rho), C.c_float(cscale), _ptr(colmax), _ptr(XS),
+                                         _ptr(alpha), _ptr(F), _ptr(q), _ptr(e), _ptr(near), _ptr(sums),
+                                         _stream(stream)))
+    return F, q, e, near, sums[:p], sums[p:2 * p], sums[2 * p:]
+
+
+def load_mlp_weights(path=None):
+    """The trained parameters shipped with the package (float32 numpy array)."""
+    p = pathlib.Path(path) if path else _HERE / "weights" / "precond_mlp.npy"
+    return np.load(p).astype(np.float32)

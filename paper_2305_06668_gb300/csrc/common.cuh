@@ -178,7 +178,7 @@ struct LockState {
 };
 void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, int nparts,
                        const double* U, double tol, int tol_kind, double tau, LockState* state,
-                       double* resnorm, double* up, bool build_p, cudaStream_t st);
+                       double* resnorm, double* colmax, double* up, bool build_p, cudaStream_t st);
 
 }  // namespace lobpcg
 

@@ -350,6 +350,7 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
                                                                int nparts, const double* __restrict__ U,
                                                                double tol, int tol_kind, double tau,
                                                                LockState* state, double* __restrict__ resnorm,
+                                                               double* __restrict__ colmax,
                                                                double* __restrict__ up, int build_p) {
   extern __shared__ double sm[];
   __shared__ double red[32];
@@ -365,6 +366,7 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
     }
     const double nr = sqrt(s2);
     resnorm[j] = nr;
+    colmax[j] = mx;
     conv[j] = tol_kind == 1 ? (nr / sqrt((double)n) <= 0.1 * tol && mx <= tol) : (nr <= tol);
   }
   if (threadIdx.x == 0) shifts = 0;
@@ -474,7 +476,7 @@ void launch_maxabs(int count, const double* C, double* out, cudaStream_t st) {
 
 void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, int nparts,
                        const double* U, double tol, int tol_kind, double tau, LockState* state,
-                       double* resnorm, double* up, bool build_p, cudaStream_t st) {
+                       double* resnorm, double* colmax, double* up, bool build_p, cudaStream_t st) {
   const size_t smem = ((size_t)2 * kMaxM * (kMaxS + 1) + (size_t)5 * kMaxM * (kMaxM + 1)) * sizeof(double);
   static bool attr = false;
   if (!attr) {
@@ -482,7 +484,7 @@ void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, 
     attr = true;
   }
   lock_p_kernel<<<1, kSmallThreads, smem, st>>>(s, m, k, n, norm_part, nparts, U, tol, tol_kind, tau,
-                                                 state, resnorm, up, build_p ? 1 : 0);
+                                                 state, resnorm, colmax, up, build_p ? 1 : 0);
   LB_LAUNCH_CHECK();
 }
 

@@ -21,6 +21,7 @@
 
 #include "../../include/lobpcg.h"
 #include "common.cuh"
+#include "mlp.cuh"
 
 using namespace lobpcg;
 
@@ -75,6 +76,7 @@ struct Stats {
   int cholqr_passes_max = 0, ortho_passes_max = 0, shifts = 0, svqb = 0, cap_hits = 0;
   int64_t spmm_columns = 0;
   int64_t spmm_launches = 0;
+  int precond_fallback = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -156,13 +158,17 @@ struct lobpcg_ctx {
   DevBuf small;  // all small FP64 matrices and partials
   double *Gpart = nullptr, *G = nullptr, *U = nullptr, *lam_all = nullptr, *up = nullptr;
   double *Tm = nullptr, *C = nullptr, *npart = nullptr, *resnorm = nullptr, *scal = nullptr;
-  double *lam = nullptr, *sgn = nullptr, *S = nullptr;
+  double *lam = nullptr, *sgn = nullptr, *S = nullptr, *colmax = nullptr;
   int* ictl = nullptr;  // [0..3] cholqr ctl, [4] sweeps, [5] finite flag
   LockState* lock = nullptr;
   DevBuf x0buf;        // column-major FP64 initial block when X0 == NULL
   double* host = nullptr;  // pinned readback area
   Stats stats;
   Profiler prof;
+  // learned preconditioner: weights (device), off-diagonal row norms rho, their mean
+  DevBuf mlp_params, rho;
+  float cscale = 0.f;
+  bool use_learned = false;  // cleared for the rest of a solve when the residuals stall
   FILE* trace = nullptr;  // per-iteration JSON lines (LOBPCG_TRACE=path)
 
   void sync() { LB_CUDA(cudaStreamSynchronize(st)); }
@@ -185,7 +191,8 @@ struct lobpcg_ctx {
     resnorm = p, p += kMaxS;
     scal = p, p += kMaxS;
     sgn = p, p += kMaxS;
-    p += 8 * kMaxS;
+    colmax = p, p += kMaxS;
+    p += 7 * kMaxS;
     ictl = reinterpret_cast<int*>(p);
     lock = reinterpret_cast<LockState*>(ictl + 32);
     LB_CUDA(cudaMallocHost(&host, 64 * kMaxS * sizeof(double)));
@@ -313,7 +320,11 @@ template <class T>
 void precondition(lobpcg_ctx& c, const T* X, const T* AX, int ld, int m_conv, int a, T* W) {
   const int pc = c.opt.precond == LOBPCG_PREC_NONE ? 0 : 1;
   c.prof.mark(PH_PRECOND);
-  launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st);
+  if (c.use_learned)
+    mlp::launch_precond_learned<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, c.rho.as<float>(), c.cscale,
+                                   c.colmax, c.mlp_params.as<float>(), W, ld, c.st);
+  else
+    launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st);
   c.prof.mark(PH_OTHER);
 }
 
@@ -367,7 +378,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     job.ld_out[0] = job.ld_out[1] = ld;
     job.nprod = 2;
     const int parts = launch_update<T>(n, job, c.U, m, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);
-    launch_lock_and_p(m, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.up,
+    launch_lock_and_p(m, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.colmax, c.up,
                       false, c.st);
   }
   cur = 1;
@@ -385,6 +396,8 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   int pw = 0;  // width of P in the current basis
   double best_rk = 1e300;
   int since_best = 0;
+  double lbest = 1e300;
+  int lsince = 0;
 
   // ---- main loop ----
   int it = 1;
@@ -409,7 +422,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     job.ld_out[0] = job.ld_out[1] = ld;
     job.nprod = 2;
     const int parts = launch_update<T>(n, job, c.U, s, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);  // X = V u_x
-    launch_lock_and_p(s, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.up,
+    launch_lock_and_p(s, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.colmax, c.up,
                       true, c.st);                                      // lock, u_p
     read_lock(m);
     c.prof.mark(PH_OTHER);
@@ -443,6 +456,14 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
         cur = nxt;
         break;
       }
+    }
+    if (c.use_learned) {
+      // the diagonal preconditioner takes over when the learned one stops making progress:
+      // the largest residual of the k sought pairs has not dropped by 10% in 20 iterations
+      double rk = 0.0;
+      for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
+      if (rk < 0.9 * lbest) lbest = rk, lsince = 0;
+      else if (++lsince >= 20) c.use_learned = false, c.stats.precond_fallback = 1;
     }
     const int a_new = ls.m_act;
     m_conv = ls.m_conv;
@@ -584,7 +605,16 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
           launch_to_float(A->n, A->dense + j * A->ld, c->dense32.as<float>() + j * A->n, c->st);
       }
     }
-    require(c->opt.precond != LOBPCG_PREC_LEARNED, "lobpcg_create: learned preconditioner not built");
+    if (c->opt.precond == LOBPCG_PREC_LEARNED) {
+      c->mlp_params.ensure(mlp::kNumParams * sizeof(float));
+      LB_CUDA(cudaMemcpyAsync(c->mlp_params.p, c->opt.mlp_weights, mlp::kNumParams * sizeof(float),
+                              cudaMemcpyHostToDevice, c->st));
+      c->rho.ensure((size_t)A->n * sizeof(float));
+      const double cs = mlp::row_norms(A->n, A->row_ptr, A->col_idx, A->val,
+                                       A->fmt == LOBPCG_DENSE ? A->dense : nullptr, A->ld, c->rho.as<float>(),
+                                       c->scal, c->st);
+      c->cscale = (float)(cs > 0 ? cs : 1.0);
+    }
     c->opt.mlp_weights = nullptr;  // not retained
     c->sync();
     return LOBPCG_OK;
@@ -606,6 +636,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     require(tol > 0 && std::isfinite(tol), "lobpcg_solve: tol must be positive");
     require(evals && evecs && resnorms, "lobpcg_solve: output pointers must not be NULL");
     c->stats = Stats{};
+    c->use_learned = c->opt.precond == LOBPCG_PREC_LEARNED;
     const long long launches0 = launch_counter();
     c->prof.begin(c->opt.profile != 0, c->st);
     const char* tr = std::getenv("LOBPCG_TRACE");
@@ -685,7 +716,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       const int parts = launch_update<double>(n, job, c->Tm, k, k, 1.0, c->lam, c->npart, c->max_ctas, c->st);
       LockState tmp{0, k, 0, 0, 0};
       LB_CUDA(cudaMemcpyAsync(c->lock, &tmp, sizeof tmp, cudaMemcpyHostToDevice, c->st));
-      launch_lock_and_p(k, k, k, n, c->npart, parts, c->Tm, tol, 0, tau, c->lock, c->resnorm, c->up, false, c->st);
+      launch_lock_and_p(k, k, k, n, c->npart, parts, c->Tm, tol, 0, tau, c->lock, c->resnorm, c->colmax, c->up, false, c->st);
     }
     launch_rows_to_colmajor<double, double>(n, k, Xs, b.ld, evecs, c->st);
     LB_CUDA(cudaMemcpyAsync(evals, c->lam, k * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -714,6 +745,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       for (int i = 0; i < 6; ++i) info->phase_seconds[i] = phases[i];
       info->kernel_launches = launch_counter() - launches0;
       info->spmm_launches = c->stats.spmm_launches;
+      info->precond_fallback = c->stats.precond_fallback;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))
@@ -732,6 +764,8 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   c->b32.buf.release();
   c->small.release();
   c->x0buf.release();
+  c->mlp_params.release();
+  c->rho.release();
   if (c->host) cudaFreeHost(c->host);
   delete c;
 }

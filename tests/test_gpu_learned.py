@@ -1,0 +1,80 @@
+"""Learned preconditioner in the solver: same eigenpairs as the oracle, and the gain of
+the trained network over the diagonal preconditioner on held-out matrices."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from tests.gpu_util import cuda, dev
+from tests.util import cluster_angles, rel_eig_err
+
+pytestmark = pytest.mark.gpu
+
+
+def _weights():
+    import paper_2305_06668_gb300 as lb
+    return lb.load_mlp_weights()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_learned_matches_oracle_eigenpairs(precision):
+    """The learned preconditioner takes a different path to the same eigenpairs than the
+    oracle's diagonal one, so the eigenvectors agree to the a-posteriori bound
+    sin(angle) <= ||r|| / gap (Davis-Kahan) of both runs, plus 1e-7."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=20_011, seed=2105)
+    x0 = synth.diag_guess(a.diag, 8, seed=2105, noise=0.0)
+    ref = oracle.lobpcg(a, a.diag, 6, x0, extra=2, tol=1e-8, maxiter=3000)
+    more = oracle.lobpcg(a, a.diag, 8, synth.diag_guess(a.diag, 10, seed=2105, noise=0.0), extra=2, tol=1e-9,
+                         maxiter=3000)  # two more eigenvalues for the gaps
+    s = lb.Solver(**lb.upload_csr(a), extra=2, precond=lb.PREC_LEARNED, mlp_weights=_weights(),
+                  precision=lb.MIXED if precision == "mixed" else lb.FP64)
+    r = s.solve(6, 1e-8, X0=torch.from_numpy(x0).cuda())
+    s.close()
+    assert ref.status == 0 and more.status == 0 and r.status == 0
+    assert np.max(rel_eig_err(r.evals, ref.evals)) <= 1e-10
+    assert np.max(rel_eig_err(more.evals[:6], ref.evals)) <= 1e-10
+    lam = more.evals
+    V = r.evecs.cpu().numpy()
+    for j in range(6):
+        gap = min(abs(lam[j] - lam[i]) for i in range(len(lam)) if i != j)
+        ang = float(cluster_angles(ref.evals[j:j + 1], ref.evecs[:, j:j + 1], V[:, j:j + 1])[0])
+        assert ang <= 1e-7 + (r.resnorms[j] + ref.resnorms[j]) / gap, (j, ang, gap)
+    assert np.max(r.resnorms) <= 1e-8
+
+
+def test_trained_network_cuts_iterations_on_heldout_ci_matrices():
+    """Held-out seeds of the CI-like family (not used in training)."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    w = _weights()
+    for seed in (2100, 2101):
+        a = synth.sparse_ci(n=100_000, seed=seed)
+        t = lb.upload_csr(a)
+        x0 = torch.from_numpy(synth.diag_guess(a.diag, 21, seed=seed, noise=0.0)).cuda()
+        out = {}
+        for name, kw in (("diag", {}), ("learned", dict(precond=lb.PREC_LEARNED, mlp_weights=w))):
+            s = lb.Solver(**t, extra=5, maxiter=4000, **kw)
+            out[name] = s.solve(16, 1e-8, X0=x0)
+            s.close()
+        d, l = out["diag"], out["learned"]
+        assert d.status == 0 and l.status == 0 and l.info["precond_fallback"] == 0
+        assert l.info["iterations"] * 3 <= d.info["iterations"], (l.info["iterations"], d.info["iterations"])
+        assert np.max(rel_eig_err(l.evals, d.evals)) <= 1e-10
+        assert np.max(l.resnorms) <= 1e-8
+
+
+def test_stalled_learned_preconditioner_falls_back_to_diagonal():
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    w = np.zeros(lb.mlp_num_params(), dtype=np.float32)
+    w[-1] = -60.0  # softplus(-60) ~ 1e-26: the learned step vanishes in the near region
+    a = synth.sparse_ci(n=20_011, seed=2105)
+    x0 = synth.diag_guess(a.diag, 8, seed=2105, noise=0.0)
+    s = lb.Solver(**lb.upload_csr(a), extra=2, precond=lb.PREC_LEARNED, mlp_weights=w, maxiter=3000)
+    r = s.solve(6, 1e-8, X0=torch.from_numpy(x0).cuda())
+    s.close()
+    assert r.status == 0 and r.info["precond_fallback"] == 1
+    ref = oracle.lobpcg(a, a.diag, 6, x0, extra=2, tol=1e-8, maxiter=3000)
+    assert np.max(rel_eig_err(r.evals, ref.evals)) <= 1e-10
