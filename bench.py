@@ -33,7 +33,10 @@ N_ROWS, K, EXTRA, TOL, SEED = 2_000_000, 16, 5, 1e-8, 0
 WORKLOAD = "CI-like sparse symmetric n=2,000,000, ~65 nnz/row, k=16 (+5 extra), tol 1e-8"
 # FP64 LOBPCG iterations this workload needs (measured with the GPU FP64 path, which takes
 # the same steps as the oracle); scales the oracle's per-iteration time of the reference arm.
-FP64_ITERATIONS_FALLBACK = 600
+FP64_ITERATIONS_FALLBACK = 1500
+# FP64 FMA throughput of this part, measured with a DFMA loop on all 152 SMs (2 FMA per
+# clock per SM at ~1.9-2.0 GHz); the peak for FP64-bound kernels.
+FP64_PEAK_TFLOPS = 1.20
 
 
 def log(*a):
@@ -220,22 +223,42 @@ def run_ours(args):
     fp64_time = r64.info["seconds"]
     fp64.close()
 
-    # dominant kernel roofline from the phase timings of the timed solves
-    peak, peak_kind = measured_peaks()
-    ph = {k: sum(i["phase_seconds"][k] for _, i, _, _ in infos) for k in lb.PHASES}
-    spmm_launches = sum(i["spmm_launches"] for _, i, _, _ in infos)
-    spmm_cols = sum(i["spmm_columns"] for _, i, _, _ in infos)
+    # rooflines of the main kernels from the phase timings of the timed solves (CUDA
+    # events on the solver stream); the dominant phase's is reported as "roofline"
+    hbm_peak, peak_kind = measured_peaks()
+    fp64_peak = FP64_PEAK_TFLOPS
+    tot = lambda key, ph: sum(i[key][ph] for _, i, _, _ in infos)
+    ph_all = {ph: tot("phase_seconds", ph) for ph in lb.PHASES}
+    ph64 = {ph: tot("phase_seconds_fp64", ph) for ph in lb.PHASES}
     nnz, n = a.nnz, a.n
-    avg_cols = spmm_cols / max(spmm_launches, 1)
-    # algorithmic bytes of one FP32 product: values + column indices + row pointers + read W + write AW
-    spmm_bytes = nnz * (4 + 4) + (n + 1) * 8 + 2 * n * avg_cols * 4
-    spmm_avg = ph["spmm"] / max(spmm_launches, 1)
-    achieved = spmm_bytes / spmm_avg / 1e9 if spmm_avg > 0 else 0.0
-    roofline = {"kernel": "spmm_csr_kernel<float> (A W, FP32 values, mixed phase)", "bound": "hbm",
-                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": None, "peak_source": peak_kind,
-                "phase_share": {k: v / max(sum(ph.values()), 1e-30) for k, v in ph.items()}}
-
+    l32 = sum(i["spmm_launches"] - i["spmm_launches_fp64"] for _, i, _, _ in infos)
+    c32 = sum(i["spmm_columns"] - i["spmm_columns_fp64"] for _, i, _, _ in infos)
+    l64 = sum(i["spmm_launches_fp64"] for _, i, _, _ in infos)
+    c64 = sum(i["spmm_columns_fp64"] for _, i, _, _ in infos)
+    rooflines = {}
+    if l32:
+        t32 = (ph_all["spmm"] - ph64["spmm"]) / l32
+        cols = c32 / l32
+        # algorithmic bytes of one FP32 product: values + column indices + row pointers + read W + write AW
+        b32 = nnz * (4 + 4) + (n + 1) * 8 + 2 * n * cols * 4
+        rooflines["spmm_fp32"] = {"kernel": "spmm_csr_band_kernel<float> (A W, mixed phase)", "bound": "hbm",
+                                  "achieved": b32 / t32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": b32 / t32 / 1e9 / hbm_peak, "traffic": None,
+                                  "bytes_per_launch": b32, "avg_launch_s": t32, "peak_source": peak_kind}
+    if l64:
+        t64 = ph64["spmm"] / l64
+        cols = c64 / l64
+        f64 = 2.0 * nnz * cols
+        rooflines["spmm_fp64"] = {"kernel": "spmm_csr_vec_kernel<double> (A W, FP64 refinement)", "bound": "alu",
+                                  "achieved": f64 / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                  "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
+                                  "flops_per_launch": f64, "avg_launch_s": t64,
+                                  "peak_source": "FP64 FMA rate measured on this GB300 (probe, 1.19-1.20 TFLOP/s)"}
+    share = {k: v / max(sum(ph_all.values()), 1e-30) for k, v in ph_all.items()}
+    dominant = max(share, key=share.get)
+    roofline = dict(rooflines.get("spmm_fp32", {}))
+    roofline["phase_share"] = share
+    roofline["dominant_phase"] = dominant
     # end to end through the C ABI from pinned host buffers: H2D of the matrix and the
     # initial block, context creation, solve, D2H of the eigenvectors
     host = {k: v.cpu().pin_memory() for k, v in t.items()}
@@ -278,8 +301,9 @@ def run_ours(args):
             "fp64_status": lb.STATUS_NAMES[r64.status], "speedup_vs_fp64": fp64_time / per_solve,
             "precond_fallback": last["precond_fallback"],
             "eig_max_rel_diff_vs_fp64": float(np.max(np.abs(infos[-1][3] - r64.evals) / np.maximum(1, np.abs(r64.evals)))),
-            "phase_seconds_per_solve": {k: v / args.steps for k, v in ph.items()},
-            "roofline": roofline, "clocks": summary,
+            "phase_seconds_per_solve": {k: v / args.steps for k, v in ph_all.items()},
+            "phase_seconds_fp64_per_solve": {k: v / args.steps for k, v in ph64.items()},
+            "roofline": roofline, "rooflines": rooflines, "clocks": summary,
             "e2e": {"value": min(e2e_times), "unit": "s", "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": int(sum(i["kernel_launches"] for _, i, _, _ in infos))}
     if base:

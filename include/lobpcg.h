@@ -118,6 +118,9 @@ typedef struct {
   int64_t kernel_launches; /* CUDA kernels this call launched */
   int64_t spmm_launches;   /* of which products with A inside the iteration */
   int precond_fallback;    /* 1 if the learned preconditioner stalled and the diagonal one took over */
+  double phase_seconds_fp64[6]; /* with opt.profile: the FP64 part of phase_seconds */
+  int64_t spmm_launches_fp64;   /* products with A in FP64 */
+  int64_t spmm_columns_fp64;    /* columns of those products */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */

@@ -49,7 +49,9 @@ class _Info(C.Structure):
                 ("cholqr_passes_max", C.c_int), ("ortho_passes_max", C.c_int), ("shifts", C.c_int),
                 ("svqb", C.c_int), ("cap_hits", C.c_int), ("spmm_columns", C.c_int64),
                 ("seconds", C.c_double), ("phase_seconds", C.c_double * 6), ("kernel_launches", C.c_int64),
-                ("spmm_launches", C.c_int64), ("precond_fallback", C.c_int)]
+                ("spmm_launches", C.c_int64), ("precond_fallback", C.c_int),
+                ("phase_seconds_fp64", C.c_double * 6), ("spmm_launches_fp64", C.c_int64),
+                ("spmm_columns_fp64", C.c_int64)]
 
 
 def library_path() -> pathlib.Path:
@@ -187,6 +189,7 @@ class Solver:
             _check(st, self._ctx)
         d = {f: getattr(info, f) for f, _ in _Info._fields_}
         d["phase_seconds"] = dict(zip(PHASES, list(info.phase_seconds)))
+        d["phase_seconds_fp64"] = dict(zip(PHASES, list(info.phase_seconds_fp64)))
         return Result(st, evals, evecs, res, d)
 
     def close(self):

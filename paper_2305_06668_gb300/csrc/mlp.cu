@@ -208,19 +208,21 @@ __global__ void precond_learned_kernel(int64_t n, const T* __restrict__ X, const
   const int rl = threadIdx.x / a_pad;
   if (j >= a) return;
   const double l = lam[c0 + j];
-  const double fl = 1e-8 * fmax(1.0, fabs(l));
+  const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
   const float g = (float)colmax[c0 + j];
+  const T lt = (T)l, band = (T)(64.0 * cscale);
   for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rl; i < n; i += (int64_t)gridDim.x * rows_per_block) {
-    const T r = AX[i * ld + c0 + j] - (T)l * X[i * ld + c0 + j];
-    const double dd = diag[i] - l;
-    double delta = dd;
-    if (fabs(delta) < fl) delta = delta >= 0.0 ? fl : -fl;
-    double scale = 1.0;
-    if (fabs(dd) <= 64.0 * cscale) {
+    const T r = AX[i * ld + c0 + j] - lt * X[i * ld + c0 + j];
+    // in the block's precision: exact for FP64, and the FP64 units stay free in the FP32 phase
+    const T dd = (T)diag[i] - lt;
+    T delta = dd;
+    if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
+    T scale = T(1);
+    if (fabs(dd) <= band) {
       const float f3 = g > 0.f ? (float)r / g : 0.f;
-      scale = softplusf(forward_z(sP, (float)(dd / (8.0 * cscale)), rho[i] / cscale, f3, h1));
+      scale = (T)softplusf(forward_z(sP, (float)dd / (float)(8.0 * cscale), rho[i] / cscale, f3, h1));
     }
-    W[i * ldw + j] = (T)((double)r * scale / delta);
+    W[i * ldw + j] = r * scale / delta;
   }
 }
 

@@ -76,6 +76,7 @@ struct Stats {
   int cholqr_passes_max = 0, ortho_passes_max = 0, shifts = 0, svqb = 0, cap_hits = 0;
   int64_t spmm_columns = 0;
   int64_t spmm_launches = 0;
+  int64_t spmm_launches64 = 0, spmm_columns64 = 0;
   int precond_fallback = 0;
 };
 
@@ -83,6 +84,7 @@ struct Stats {
 enum Phase { PH_SPMM = 0, PH_RR_GRAM, PH_RR_EIG, PH_UPDATE, PH_PRECOND, PH_ORTHO, PH_OTHER, PH_COUNT };
 struct Profiler {
   bool on = false;
+  int prec64 = 1;  // precision of the phases being marked (1: FP64, 0: FP32)
   cudaStream_t st = nullptr;
   std::vector<cudaEvent_t> pool;
   std::vector<int> phase;
@@ -101,17 +103,20 @@ struct Profiler {
       pool.push_back(e);
     }
     LB_CUDA(cudaEventRecord(pool[used], st));
-    phase.push_back(ph);
+    phase.push_back(ph + (prec64 ? PH_COUNT : 0));
     ++used;
   }
-  void finish(double* out) {
-    for (int i = 0; i < PH_COUNT; ++i) out[i] = 0.0;
+  // out[0..PH_COUNT) all phases, out64[0..PH_COUNT) the FP64 part
+  void finish(double* out, double* out64) {
+    for (int i = 0; i < PH_COUNT; ++i) out[i] = out64[i] = 0.0;
     if (!on || used < 2) return;
     LB_CUDA(cudaStreamSynchronize(st));
     for (size_t i = 0; i + 1 < used; ++i) {
       float ms = 0.f;
       LB_CUDA(cudaEventElapsedTime(&ms, pool[i], pool[i + 1]));
-      out[phase[i]] += ms * 1e-3;
+      const int ph = phase[i] % PH_COUNT;
+      out[ph] += ms * 1e-3;
+      if (phase[i] >= PH_COUNT) out64[ph] += ms * 1e-3;
     }
   }
   ~Profiler() {
@@ -230,6 +235,7 @@ void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
     launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
   c.stats.spmm_columns += p;
   c.stats.spmm_launches += 1;
+  if (sizeof(T) == 8) c.stats.spmm_launches64 += 1, c.stats.spmm_columns64 += p;
   c.prof.mark(PH_OTHER);
 }
 
@@ -343,6 +349,7 @@ template <class T>
 PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int maxiter, bool stall_exit,
                     double switch_tol = 0.0) {
   Blocks<T>& b = Prec<T>::blocks(c);
+  c.prof.prec64 = sizeof(T) == 8 ? 1 : 0;
   const int64_t n = c.A.n;
   const int ld = b.ld;
   const int cap = c.opt.ortho_cap, cap2 = c.opt.ortho2_cap;
@@ -702,6 +709,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     apply_A<double>(*c, Xs, b.ld, k, AXs, b.ld);
     c->stats.spmm_columns -= k;  // the check product is not part of the iteration
     c->stats.spmm_launches -= 1;
+    c->stats.spmm_launches64 -= 1, c->stats.spmm_columns64 -= k;
     {
       // residual norms of the normalised vectors: out = in * I (reuse the update epilogue)
       std::vector<double> eye((size_t)k * k, 0.0);
@@ -727,8 +735,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     LB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    double phases[PH_COUNT];
-    c->prof.finish(phases);
+    double phases[PH_COUNT], phases64[PH_COUNT];
+    c->prof.finish(phases, phases64);
     if (c->trace) std::fclose(c->trace);
     c->trace = nullptr;
     if (info) {
@@ -742,7 +750,9 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->cap_hits = c->stats.cap_hits;
       info->spmm_columns = c->stats.spmm_columns;
       info->seconds = ms * 1e-3;
-      for (int i = 0; i < 6; ++i) info->phase_seconds[i] = phases[i];
+      for (int i = 0; i < 6; ++i) info->phase_seconds[i] = phases[i], info->phase_seconds_fp64[i] = phases64[i];
+      info->spmm_launches_fp64 = c->stats.spmm_launches64;
+      info->spmm_columns_fp64 = c->stats.spmm_columns64;
       info->kernel_launches = launch_counter() - launches0;
       info->spmm_launches = c->stats.spmm_launches;
       info->precond_fallback = c->stats.precond_fallback;

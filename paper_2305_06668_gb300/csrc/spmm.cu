@@ -249,7 +249,7 @@ __device__ __forceinline__ void stage_csr(const int32_t* __restrict__ ci, const 
 // double-buffered in shared memory with cp.async, so the HBM stream of the matrix stays
 // in flight while the warps gather from shared memory.  A sub-block with more than `cap`
 // non-zeros is read straight from global memory.
-template <class T, class V, int L, int UNR, int RS>
+template <class T, class V, int L, int UNR, int RS, int NV>
 __global__ void __launch_bounds__(512) spmm_csr_band_kernel(int64_t n, const int64_t* __restrict__ rp,
                                                             const int32_t* __restrict__ ci,
                                                             const V* __restrict__ val, int p,
@@ -290,8 +290,12 @@ __global__ void __launch_bounds__(512) spmm_csr_band_kernel(int64_t n, const int
   }
   asm volatile("cp.async.commit_group;\n" ::);
   const int g = lane / L, li = lane % L;
-  const int col0 = li * VEC;
+  const int col0 = li * VEC * NV;  // each lane owns NV consecutive 16-byte vectors of a row
   const bool has_cols = col0 < p;
+  const T* tile_c = tile + col0;
+  const T* X_c = X + col0;
+  const unsigned uwin = (unsigned)win;
+  const int ilo = (int)lo;
   for (int k = 0; k < nsub; ++k) {
     const int buf = k & 1;
     int64_t eb, ee;
@@ -306,51 +310,61 @@ __global__ void __launch_bounds__(512) spmm_csr_band_kernel(int64_t n, const int
     asm volatile("cp.async.commit_group;\n" ::);
     asm volatile("cp.async.wait_group 1;\n" ::);
     __syncthreads();
-    const int32_t* sc = scol + buf * cap;
-    const V* sv = sval + buf * cap;
+    // column indices / values of this sub-block: shared memory, or global memory when the
+    // sub-block was too large to stage (both indexed by e - eb)
+    const int32_t* sc = staged ? scol + buf * cap : ci + eb;
+    const V* sv = staged ? sval + buf * cap : val + eb;
     const int64_t rb = r0 + (int64_t)k * RS, re = min(r_end, rb + RS);
     for (int64_t row = rb + wid; row < re; row += wpc) {
-      const int64_t e0 = rp[row], e1 = rp[row + 1];
-      T acc[VEC];
+      const int le0 = (int)(rp[row] - eb), le1 = (int)(rp[row + 1] - eb);
+      T acc[NV][VEC];
 #pragma unroll
-      for (int t = 0; t < VEC; ++t) acc[t] = T(0);
-      for (int64_t j = e0; j < e1; j += G * UNR) {
-        VT xv[UNR];
+      for (int w = 0; w < NV; ++w)
+#pragma unroll
+        for (int t = 0; t < VEC; ++t) acc[w][t] = T(0);
+      for (int lj = le0; lj < le1; lj += G * UNR) {
+        VT xv[UNR][NV];
         T vv[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
-          const int64_t e = j + u * G + g;
-          xv[u] = VT{};
-          vv[u] = T(0);
-          if (e < e1) {
-            const int cc = staged ? sc[e - eb] : ci[e];
-            const T w = staged ? (T)sv[e - eb] : (T)val[e];
-            if (has_cols) {
-              vv[u] = w;
-              if (cc >= lo && cc < hi) xv[u] = *reinterpret_cast<const VT*>(tile + (int64_t)(cc - lo) * pp + col0);
-              else xv[u] = *reinterpret_cast<const VT*>(X + (int64_t)cc * ldx + col0);
-            }
-          }
+          const int le = lj + u * G + g;
+          const bool valid = le < le1 && has_cols;
+          const int c = valid ? sc[le] : ilo;
+          vv[u] = valid ? (T)sv[le] : T(0);
+          // band couplings read the shared-memory window, the others global memory; one
+          // generic load for both keeps the lanes of a warp on one path
+          const unsigned o = (unsigned)(c - ilo);
+          const VT* src = reinterpret_cast<const VT*>(o < uwin ? tile_c + (int64_t)o * pp : X_c + (int64_t)c * ldx);
+#pragma unroll
+          for (int w = 0; w < NV; ++w) xv[u][w] = valid ? src[w] : VT{};
         }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) vfma(vv[u], xv[u], acc);
+        for (int u = 0; u < UNR; ++u)
+#pragma unroll
+          for (int w = 0; w < NV; ++w) vfma(vv[u], xv[u][w], acc[w]);
       }
 #pragma unroll
-      for (int t = 0; t < VEC; ++t)
+      for (int w = 0; w < NV; ++w)
 #pragma unroll
-        for (int o = L; o < kWarp; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+        for (int t = 0; t < VEC; ++t)
+#pragma unroll
+          for (int o = L; o < kWarp; o <<= 1) acc[w][t] += __shfl_xor_sync(0xffffffffu, acc[w][t], o);
       if (g == 0 && has_cols) {
         T* yr = Y + row * ldy + col0;
-        if (col0 + VEC <= p) {
-          VT out;
-          T* po = reinterpret_cast<T*>(&out);
 #pragma unroll
-          for (int t = 0; t < VEC; ++t) po[t] = acc[t];
-          *reinterpret_cast<VT*>(yr) = out;
-        } else {
+        for (int w = 0; w < NV; ++w) {
+          const int cw = col0 + w * VEC;
+          if (cw + VEC <= p) {
+            VT out;
+            T* po = reinterpret_cast<T*>(&out);
 #pragma unroll
-          for (int t = 0; t < VEC; ++t)
-            if (col0 + t < p) yr[t] = acc[t];
+            for (int t = 0; t < VEC; ++t) po[t] = acc[w][t];
+            *reinterpret_cast<VT*>(yr + w * VEC) = out;
+          } else {
+#pragma unroll
+            for (int t = 0; t < VEC; ++t)
+              if (cw + t < p) yr[w * VEC + t] = acc[w][t];
+          }
         }
       }
     }
@@ -359,12 +373,13 @@ __global__ void __launch_bounds__(512) spmm_csr_band_kernel(int64_t n, const int
   asm volatile("cp.async.wait_group 0;\n" ::);
 }
 
-template <class T, class V, int L>
+template <class T, class V, int L, int NV>
 bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
                      T* Y, int ldy, int band, cudaStream_t st) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int RS = 64;
-  const int pp = round_up(p, VEC);
+  const int pp = round_up(p, VEC * NV);
+  if (ldx < pp) return false;  // the window rows and X rows are read NV vectors at a time
   const size_t row_bytes = (size_t)pp * sizeof(T);
   const int cap = 5120;  // non-zeros per staged sub-block of RS rows (about 33 KB of the matrix in flight)
   const size_t csr_bytes = (size_t)2 * cap * (sizeof(V) + sizeof(int32_t));
@@ -378,16 +393,16 @@ bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   const int64_t win = std::min<int64_t>(n, R + 2 * (int64_t)band);
   const size_t smem = (size_t)win * row_bytes + csr_bytes;
   if (smem > 220 * 1024) return false;
-  constexpr int UNR = (L < 8 ? L : 8);
+  constexpr int UNR = (L < 4 ? L : 4);
   static bool attr = false;
   if (!attr) {
-    LB_CUDA(cudaFuncSetAttribute(spmm_csr_band_kernel<T, V, L, UNR, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    LB_CUDA(cudaFuncSetAttribute(spmm_csr_band_kernel<T, V, L, UNR, RS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  225 * 1024));
     attr = true;
   }
   const int64_t ctas = ceil_div(n, R);
-  spmm_csr_band_kernel<T, V, L, UNR, RS><<<(unsigned)ctas, 512, smem, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy, (int)R,
-                                                                          band, pp, cap);
+  spmm_csr_band_kernel<T, V, L, UNR, RS, NV><<<(unsigned)ctas, 512, smem, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy,
+                                                                              (int)R, band, pp, cap);
   LB_LAUNCH_CHECK();
   return true;
 }
@@ -464,13 +479,14 @@ void launch_spmm_csr(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   const bool vec_ok = (ldx % VEC == 0) && (ldy % VEC == 0) && ldx >= round_up(p, VEC) &&
                       !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15);
   if (vec_ok && band >= 0) {
-    const int lanes = (p + VEC - 1) / VEC;
+    // two 16-byte vectors per lane halve the index work per gathered value
+    const int lanes = (p + 2 * VEC - 1) / (2 * VEC);
     bool done = false;
-    if (lanes <= 1) done = csr_band_launch<T, V, 1>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 2) done = csr_band_launch<T, V, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 4) done = csr_band_launch<T, V, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 8) done = csr_band_launch<T, V, 8>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else done = csr_band_launch<T, V, 16>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    if (lanes <= 1) done = csr_band_launch<T, V, 1, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    else if (lanes <= 2) done = csr_band_launch<T, V, 2, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    else if (lanes <= 4) done = csr_band_launch<T, V, 4, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    else if (lanes <= 8) done = csr_band_launch<T, V, 8, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    else done = csr_band_launch<T, V, 16, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
     if (done) return;
   }
   if (vec_ok) {
