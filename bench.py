@@ -314,6 +314,60 @@ def run_ours(args):
     return 0
 
 
+def run_batched(args):
+    """The batched serving workload (a separate line, not the headline): 256 problems of the
+    cfg1 construction, n ~ U[10,000, 500,000], k ~ U{1..32}, generated on the GPU; all
+    solved with lobpcg_solve_batched (mixed precision + FP64 refinement, one stream per
+    problem) against the same problems solved one by one with the plain FP64 path."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_06668_gb300 as lb
+    import synth
+    specs = synth.batched_specs(args.nprob, seed=0)
+    mats, x0s = [], []
+    for n, k, sd in specs:
+        t = synth.sparse_cfg1_torch(n, sd)
+        mats.append(t)
+        x0s.append(synth.diag_guess_torch(t["diag"], k))
+    torch.cuda.synchronize()
+    ks = [k for _, k, _ in specs]
+    streams = [torch.cuda.Stream() for _ in specs]
+    batched = [lb.Solver(**t, precision=lb.MIXED, stream=st) for t, st in zip(mats, streams)]
+    times = []
+    for rep in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rb = lb.solve_batched(batched, ks, [TOL] * len(ks), x0s, nthreads=args.threads)
+        torch.cuda.synchronize()
+        if rep >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    torch.cuda.synchronize()
+    # one by one with the plain FP64 path: context creation, solve, release per problem
+    seq = 0.0
+    r1 = []
+    for t, k, x in zip(mats, ks, x0s):
+        s = lb.Solver(**t, precision=lb.FP64)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r1.append(s.solve(k, TOL, X0=x))
+        torch.cuda.synchronize()
+        seq += time.perf_counter() - t0
+        s.close()
+    diff = max(float(np.max(np.abs(a.evals - b.evals) / np.maximum(1, np.abs(b.evals)))) for a, b in zip(rb, r1))
+    line = {"metric": "time to solve 256 independent problems at \u2016r\u2016\u22641e-8 (batched)",
+            "value": min(times), "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "higher_is_better": False, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"{len(specs)} cfg1-recipe problems, n ~ U[10k, 500k], k ~ U{{1..32}}",
+                       "sum_n": int(sum(n for n, _, _ in specs)), "sum_nnz": int(sum(int(t['row_ptr'][-1]) for t in mats)),
+                       "form": "lobpcg_solve_batched, mixed precision + FP64 refinement, one stream per problem"},
+            "sequential_plain_fp64_s": seq, "speedup_vs_sequential_fp64": seq / min(times),
+            "status_ok": sum(r.status == lb.OK for r in rb), "max_rel_eig_diff_vs_fp64": diff,
+            "iterations_total": int(sum(r.info["iterations"] for r in rb))}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,7 +376,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched"],
+                    help="ci2m: the headline workload; batched: the 256-problem serving workload")
+    ap.add_argument("--nprob", type=int, default=256)
+    ap.add_argument("--threads", type=int, default=32)
     args = ap.parse_args()
+    if args.config == "batched":
+        return run_batched(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -150,6 +150,21 @@ LOBPCG_API lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
 LOBPCG_API lobpcg_status lobpcg_solve(lobpcg_ctx* ctx, int k, double tol, const double* X0, double* evals,
                            double* evecs, double* resnorms, lobpcg_info* info);
 
+/* Solves nprob independent problems concurrently (the batched serving form; not in the
+ * paper).  ctxs[i] is a context from lobpcg_create; give each its own stream so that the
+ * problems' kernels run side by side.  A pool of nthreads host threads (<= 0: 32) runs
+ * lobpcg_solve(ctxs[i], k[i], tol[i], X0 ? X0[i] : NULL, evals[i], evecs[i],
+ * resnorms[i], infos ? &infos[i] : NULL), largest problems first; statuses[i] receives
+ * each result.  Every problem's arithmetic is exactly that of lobpcg_solve, so the
+ * results equal one-by-one solves.  Each context releases its block workspace when its
+ * problem is done, so only the problems in flight hold it.  Returns OK when every
+ * problem returned OK, else the first non-OK status in problem order.  Contexts must be
+ * distinct. */
+LOBPCG_API lobpcg_status lobpcg_solve_batched(lobpcg_ctx* const* ctxs, int nprob, const int* k, const double* tol,
+                                              const double* const* X0, double* const* evals, double* const* evecs,
+                                              double* const* resnorms, lobpcg_info* infos, lobpcg_status* statuses,
+                                              int nthreads);
+
 /* Releases the context and everything it owns.  NULL-safe. */
 LOBPCG_API void lobpcg_destroy(lobpcg_ctx* ctx);
 

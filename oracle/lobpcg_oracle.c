@@ -38,6 +38,28 @@
  *      u_p = ortho(u~_p; u_x) in R^s with Algorithm 3.
  *  R9  The Rayleigh-Ritz matrix is symmetrised as (a + a^T) / 2 before the eigensolve.
  *  R10 Reported residual norms are recomputed with a fresh product A X at exit.
+ *  R15 Algorithm 2 factors the diagonally scaled overlap D M D, D = diag(M)^{-1/2}, and
+ *      sets X <- X D L^{-T} (scaled Cholesky-QR).  In exact arithmetic this is the same Q
+ *      (the QR factor of X D equals that of X); in floating point it makes the shift of
+ *      R4 (now 100 eps trace(D M D) = 100 eps p) relative to unit columns, so a column
+ *      whose norm is at the rounding level of the others is still normalised.  Without
+ *      it such a column (a P direction of a Ritz vector that did not move) stays
+ *      unnormalised through every pass and breaks the orthonormality of V.
+ *  R16 When ortho(W~; Y) stops at its pass cap, the columns of W whose largest overlap
+ *      with Y is still above sqrt(tau) are dropped from W (W then has fewer than m_act
+ *      columns).  Such a column's direction was (to rounding) already in span(Y), so
+ *      the search space loses nothing; kept, it would make V rank-deficient and give a
+ *      spurious Ritz value with a vanishing vector.  The same rule, plus a unit-norm
+ *      check, is applied to u_p in R^s: when a column was unlocked since the previous
+ *      step, more P directions are asked for than the complement of u_x in R^s holds
+ *      (s - m of them), and the surplus column cannot be made orthogonal.
+ *  R14 A P direction exists only where x_j moved: the coefficient vector u~_p of column j,
+ *      after projecting out u_x, is (I - u_x u_x^T) e_j; when it vanishes exactly (norm
+ *      <= 1e-200, e.g. when the Rayleigh-Ritz coupling of a localised vector is exactly
+ *      zero and its Jacobi column stays e_j) the column is dropped from P (P then has fewer
+ *      than m_act columns).  A zero vector cannot be normalised by Algorithm 2, and in V it
+ *      would produce a spurious Ritz value 0 with a zero "residual".  Columns that are
+ *      merely small (rounding noise) are kept, as the printed algorithm does.
  */
 #include "lobpcg_oracle.h"
 
@@ -291,26 +313,37 @@ int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, 
       break;
     }
     ++passes;
-    memcpy(L, M, sizeof(double) * (size_t)p * p);
+    /* scaled overlap D M D, D = diag(M)^{-1/2}  (R15) */
+    double* Dv = (double*)malloc(sizeof(double) * (size_t)p);
+    double* Ms = (double*)malloc(sizeof(double) * (size_t)p * p);
+    for (int i = 0; i < p; ++i) Dv[i] = M[i + i * p] > 0.0 ? 1.0 / sqrt(M[i + i * p]) : 1.0;
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i) Ms[i + j * p] = Dv[i] * M[i + j * p] * Dv[j];
+    memcpy(L, Ms, sizeof(double) * (size_t)p * p);
     int fail = oracle_cholesky(p, L);
     if (fail) {
       /* level shift (Sec. 3.2), grown by 10x until the factorisation succeeds */
       double tr = 0.0;
-      for (int i = 0; i < p; ++i) tr += M[i + i * p];
+      for (int i = 0; i < p; ++i) tr += Ms[i + i * p];
       double sigma = 100.0 * EPS * tr;
       for (int t = 0; t < 8 && fail; ++t, sigma *= 10.0) {
-        memcpy(L, M, sizeof(double) * (size_t)p * p);
+        memcpy(L, Ms, sizeof(double) * (size_t)p * p);
         for (int i = 0; i < p; ++i) L[i + i * p] += sigma;
         if (shifts) ++*shifts;
         fail = oracle_cholesky(p, L);
       }
     }
+    free(Ms);
     if (fail) {
+      free(Dv);
       if (svqb) ++*svqb;
       oracle_svqb(n, p, X, M);
       continue;
     }
-    right_solve_lower_transpose(n, p, X, L); /* X <- X L^{-T} */
+    for (int j = 0; j < p; ++j)
+      for (int64_t i = 0; i < n; ++i) X[i + (int64_t)j * n] *= Dv[j];
+    free(Dv);
+    right_solve_lower_transpose(n, p, X, L); /* X <- X D L^{-T} */
   }
   if (passes_max && passes > *passes_max) *passes_max = passes;
   free(M);
@@ -341,6 +374,27 @@ int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, do
   }
   free(C);
   return passes;
+}
+
+/* R16: after ortho(W~; Y), drop the columns of W whose overlap with Y is still above
+ * sqrt(tau) (and, with check_norm, whose norm is not 1 to sqrt(tau)); the kept columns
+ * are packed to the front.  Returns their number. */
+static int drop_unorthogonal_columns(int64_t n, int p, double* W, int q, const double* Y, double tau,
+                                     int check_norm) {
+  if (q <= 0 || p <= 0) return p;
+  double* Cm = (double*)malloc(sizeof(double) * (size_t)q * p);
+  oracle_gram(n, q, Y, p, W, Cm);
+  int kept = 0;
+  for (int j = 0; j < p; ++j) {
+    const double worst = max_abs(q, Cm + (size_t)j * q);
+    const double nrm = sqrt(pairwise_dot(W + (size_t)j * n, W + (size_t)j * n, n));
+    if (worst <= sqrt(tau) && (!check_norm || fabs(nrm - 1.0) <= sqrt(tau))) {
+      if (kept != j) memcpy(W + (size_t)kept * n, W + (size_t)j * n, sizeof(double) * n);
+      ++kept;
+    }
+  }
+  free(Cm);
+  return kept;
 }
 
 /* ------------------------------------------------------------- Algorithm 1 (Sec. 3.1) */
@@ -478,25 +532,27 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     goto done;
   }
   precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);          /* W~ = T R */
+  int w_cols = m_act; /* columns of W (R16) */
   {
     int p2 = oracle_ortho_against(n, m_act, W, m, X, tau, cap, cap2, &loc.shifts, &loc.svqb,
                                   &loc.cap_hits, &loc.cholqr_passes_max); /* W = ortho(W~; X) */
     if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;
+    w_cols = drop_unorthogonal_columns(n, m_act, W, m, X, tau, 0);
   }
-  oracle_apply(A, m_act, W, AW);                                          /* AW = A W */
-  loc.spmm_columns += m_act;
+  oracle_apply(A, w_cols, W, AW);                                         /* AW = A W */
+  loc.spmm_columns += w_cols;
 
   /* ---- Algorithm 1, main loop ---- */
   for (it = 1; it <= opt->maxiter; ++it) {
     /* expansion subspace: V = (X, W) on the first pass, (X, W, P) afterwards */
-    const int s = m + m_act + (have_p ? m_act : 0);
+    const int s = m + w_cols + have_p;
     memcpy(V, X, sizeof(double) * n * m);
-    memcpy(V + n * m, W, sizeof(double) * n * m_act);
+    memcpy(V + n * m, W, sizeof(double) * n * w_cols);
     memcpy(AV, AX, sizeof(double) * n * m);
-    memcpy(AV + n * m, AW, sizeof(double) * n * m_act);
+    memcpy(AV + n * m, AW, sizeof(double) * n * w_cols);
     if (have_p) {
-      memcpy(V + n * (m + m_act), P, sizeof(double) * n * m_act);
-      memcpy(AV + n * (m + m_act), AP, sizeof(double) * n * m_act);
+      memcpy(V + n * (m + w_cols), P, sizeof(double) * n * have_p);
+      memcpy(AV + n * (m + w_cols), AP, sizeof(double) * n * have_p);
     }
     oracle_gram(n, s, V, s, AV, a);                                       /* a = V^T AV */
     for (int j = 0; j < s; ++j)
@@ -515,30 +571,46 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
       status = ORACLE_OK;
       break;
     }
-    /* P coefficients: u~_p = u_x[:, act] - E_act, u_p = ortho(u~_p; u_x)  (R8) */
+    /* P coefficients: u~_p = u_x[:, act] - E_act, u_p = ortho(u~_p; u_x)  (R8, R14) */
+    int p_cols = 0;
     for (int c = 0; c < m_act; ++c) {
       int j = m_conv + c;
-      memcpy(up + (size_t)c * s, U + (size_t)j * s, sizeof(double) * s);
-      up[j + (size_t)c * s] -= 1.0;
+      double* col = up + (size_t)p_cols * s;
+      memcpy(col, U + (size_t)j * s, sizeof(double) * s);
+      col[j] -= 1.0;
+      /* norm of (I - u_x u_x^T) u~_p_j: keep the column only if x_j moved */
+      double* proj = (double*)malloc(sizeof(double) * s);
+      memcpy(proj, col, sizeof(double) * s);
+      for (int q = 0; q < m; ++q) {
+        double d = 0.0;
+        for (int i = 0; i < s; ++i) d += U[i + (size_t)q * s] * col[i];
+        for (int i = 0; i < s; ++i) proj[i] -= d * U[i + (size_t)q * s];
+      }
+      double nrm = 0.0;
+      for (int i = 0; i < s; ++i) nrm += proj[i] * proj[i];
+      free(proj);
+      if (sqrt(nrm) > 1e-200) ++p_cols;
     }
-    {
-      int p2 = oracle_ortho_against(s, m_act, up, m, U, tau, cap, cap2, &loc.shifts,
+    if (p_cols > 0) {
+      int p2 = oracle_ortho_against(s, p_cols, up, m, U, tau, cap, cap2, &loc.shifts,
                                     &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
       (void)p2;
+      p_cols = drop_unorthogonal_columns(s, p_cols, up, m, U, tau, 1); /* R16 in R^s */
     }
-    block_times_small(n, s, V, m_act, up, P);                             /* P = V u_p, AP = AV u_p */
-    block_times_small(n, s, AV, m_act, up, AP);
-    have_p = 1;
+    block_times_small(n, s, V, p_cols, up, P);                            /* P = V u_p, AP = AV u_p */
+    block_times_small(n, s, AV, p_cols, up, AP);
+    have_p = p_cols;
     precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
     memcpy(Y, X, sizeof(double) * n * m);                                 /* Y = (X, P) */
-    memcpy(Y + n * m, P, sizeof(double) * n * m_act);
+    memcpy(Y + n * m, P, sizeof(double) * n * have_p);
     {
-      int p2 = oracle_ortho_against(n, m_act, W, m + m_act, Y, tau, cap, cap2, &loc.shifts,
+      int p2 = oracle_ortho_against(n, m_act, W, m + have_p, Y, tau, cap, cap2, &loc.shifts,
                                     &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
       if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;           /* W = ortho(W~; (X, P)) */
+      w_cols = drop_unorthogonal_columns(n, m_act, W, m + have_p, Y, tau, 0); /* R16 */
     }
-    oracle_apply(A, m_act, W, AW);                                        /* AW = A W */
-    loc.spmm_columns += m_act;
+    oracle_apply(A, w_cols, W, AW);                                       /* AW = A W */
+    loc.spmm_columns += w_cols;
   }
   if (it > opt->maxiter) it = opt->maxiter;
 

@@ -69,7 +69,7 @@ def lib():
                      "lobpcg_spmm_dense_f64", "lobpcg_gram_f64", "lobpcg_syev_f64", "lobpcg_ortho_f64",
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
-                     "lobpcg_row_norms", "lobpcg_mlp_num_params"):
+                     "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -191,6 +191,10 @@ class Solver:
         d["phase_seconds"] = dict(zip(PHASES, list(info.phase_seconds)))
         d["phase_seconds_fp64"] = dict(zip(PHASES, list(info.phase_seconds_fp64)))
         return Result(st, evals, evecs, res, d)
+
+    @property
+    def handle(self):
+        return self._ctx
 
     def close(self):
         if getattr(self, "_ctx", None) and self._ctx.value:
@@ -364,3 +368,47 @@ def load_mlp_weights(path=None):
     """The trained parameters shipped with the package (float32 numpy array)."""
     p = pathlib.Path(path) if path else _HERE / "weights" / "precond_mlp.npy"
     return np.load(p).astype(np.float32)
+
+
+def solve_batched(solvers, ks, tols, X0s=None, nthreads=32):
+    """Solve independent problems concurrently (lobpcg_solve_batched).
+
+    solvers: list of Solver (each with its own CUDA stream); ks, tols: per problem;
+    X0s: optional list of initial blocks (CUDA float64, n x (k + extra)) or None.
+    Returns a list of Result in problem order."""
+    torch = _torch()
+    nprob = len(solvers)
+    ctxs = (C.c_void_p * nprob)(*[s.handle.value for s in solvers])
+    karr = (C.c_int * nprob)(*ks)
+    tarr = (C.c_double * nprob)(*tols)
+    keep = []
+    x0p = None
+    if X0s is not None:
+        cols = []
+        for s, k, X in zip(solvers, ks, X0s):
+            if X is None:
+                cols.append(None)
+                continue
+            Xc = X.t().contiguous().t()
+            keep.append(Xc)
+            cols.append(Xc.data_ptr())
+        x0p = (C.c_void_p * nprob)(*cols)
+    evals = [np.zeros(k) for k in ks]
+    res = [np.zeros(k) for k in ks]
+    vecs = [torch.empty((k, s.n), dtype=torch.float64, device="cuda").t() for s, k in zip(solvers, ks)]
+    ev_p = (C.c_void_p * nprob)(*[e.ctypes.data for e in evals])
+    rs_p = (C.c_void_p * nprob)(*[r.ctypes.data for r in res])
+    vc_p = (C.c_void_p * nprob)(*[v.data_ptr() for v in vecs])
+    infos = (_Info * nprob)()
+    st = (C.c_int * nprob)()
+    torch.cuda.synchronize()
+    lib().lobpcg_solve_batched(ctxs, C.c_int(nprob), karr, tarr, x0p, ev_p, vc_p, rs_p, infos, st, C.c_int(nthreads))
+    out = []
+    for i in range(nprob):
+        d = {f: getattr(infos[i], f) for f, _ in _Info._fields_}
+        d["phase_seconds"] = dict(zip(PHASES, list(infos[i].phase_seconds)))
+        d["phase_seconds_fp64"] = dict(zip(PHASES, list(infos[i].phase_seconds_fp64)))
+        if st[i] not in (OK, ENOCONV):
+            raise LobpcgError(st[i], lib().lobpcg_last_error(solvers[i].handle).decode())
+        out.append(Result(st[i], evals[i], vecs[i], res[i], d))
+    return out

@@ -340,11 +340,12 @@ int gram_launch(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper, doubl
   const size_t stage = (size_t)R * (pa_pad + pb_pad) * sizeof(T);
   const size_t red = (size_t)groups * ntiles * per * sizeof(double);
   const size_t smem = std::max(stage, red);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(gram_kernel<T, TI, TJ, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   // rows per CTA: multiple of R, at most max_ctas CTAs
   int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
   if (ctas < 1) ctas = 1;
@@ -386,11 +387,12 @@ int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, in
   const int rows_per_pass = threads / tpr;
   const size_t smem = (size_t)s * qpad * sizeof(T) + (size_t)job.nprod * R * s * sizeof(T) +
                       (norm_part ? (size_t)rows_per_pass * 2 * qpad * sizeof(double) : 0) + 16;
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(update_kernel<T, CJ, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
   if (ctas < 1) ctas = 1;
   const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;

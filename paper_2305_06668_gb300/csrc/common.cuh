@@ -163,18 +163,22 @@ void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U
 //  attempts, ctl[2] += 1 if SVQB had to be used (then Linv holds the SVQB transform).
 void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl,
                          cudaStream_t st);
+// max |C - I| over a p x p matrix -> *out (device double)
+void launch_maxabs_minus_identity(int p, const double* C, double* out, cudaStream_t st);
 // max |C| over a p x q matrix -> *out (device double)
 void launch_maxabs(int count, const double* C, double* out, cudaStream_t st);
 
 // Lock decision + P coefficients (Algorithm 1, lock and u_p steps):
 //  reads norm partials (nparts x 2m), lam (m), U (s x s), state -> writes resnorm (m),
-//  new m_conv / m_act, done flag, and u_p (s x m_act) = ortho(u_x[:,act] - E_act; u_x).
+//  new m_conv / m_act, done flag, and u_p (s x p_cols) = ortho(u~_p; u_x) over the active
+//  columns whose projected coefficient vector is not negligible (state->p_cols of them).
 struct LockState {
   int m_conv;
   int m_act;
   int done;
   int sp_shifts;
   int sp_passes;
+  int p_cols;  // columns of u_p (the active ones whose Ritz vector moved)
 };
 void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, int nparts,
                        const double* U, double tol, int tol_kind, double tau, LockState* state,

@@ -307,11 +307,12 @@ void launch_backward(int64_t N, const float* F, const float* P, const float* g, 
                      cudaStream_t st) {
   if (N <= 0) return;
   const size_t smem = (size_t)(kNumParams + 3 + 4 * TB * (H + 1) + TB * 3 + TB) * sizeof(float);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(backward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   backward_kernel<<<(unsigned)std::min<int64_t>(ceil_div(N, TB), 152 * 4), TB, smem, st>>>(N, F, P, g, grad, b);
   LB_LAUNCH_CHECK();
 }

@@ -281,9 +281,22 @@ __global__ void __launch_bounds__(kSmallThreads) cholqr_small_kernel(int p, cons
     if (threadIdx.x == 0) ctl[0] = 1;
     return;
   }
-  const int fail = shifted_chol_cta(p, M, ld, L, ld, &flag, &shifts, red);
+  // scaled Cholesky-QR: factor D M D with D = diag(M)^{-1/2}, transform T = D L^{-T}
+  for (int i = threadIdx.x; i < p; i += blockDim.x) theta[i] = M[i + i * ld] > 0.0 ? rsqrt(M[i + i * ld]) : 1.0;
+  __syncthreads();
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int i = e % p, j = e / p;
+    Z[i + j * ld] = theta[i] * M[i + j * ld] * theta[j];
+  }
+  __syncthreads();
+  const int fail = shifted_chol_cta(p, Z, ld, L, ld, &flag, &shifts, red);
   if (!fail) {
     inv_lower_transpose_cta(p, L, ld, T, ld);
+    for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+      const int i = e % p, j = e / p;
+      T[i + j * ld] *= theta[i];
+    }
+    __syncthreads();
   } else {
     svqb_cta(p, M, ld, L, Z, ld, T, ld, rot, red, theta);
   }
@@ -328,9 +341,22 @@ __device__ void small_ortho(int s, int a, double* X, int ldx, double tau, int ca
     }
     dev = block_max(dev, red);
     if (dev <= tau || pass >= cap) return;
-    const int fail = shifted_chol_cta(a, M, ld, L, ld, flag, shifts, red);
-    if (!fail) inv_lower_transpose_cta(a, L, ld, Tm, ld);
-    else svqb_cta(a, M, ld, L, Z, ld, Tm, ld, rot, red, theta);
+    // scaled Cholesky-QR (D M D, D = diag(M)^{-1/2}), as in the n-dimensional ortho
+    for (int i = threadIdx.x; i < a; i += blockDim.x) theta[i] = M[i + i * ld] > 0.0 ? rsqrt(M[i + i * ld]) : 1.0;
+    __syncthreads();
+    for (int e = threadIdx.x; e < a * a; e += blockDim.x) {
+      const int i = e % a, j = e / a;
+      Z[i + j * ld] = theta[i] * M[i + j * ld] * theta[j];
+    }
+    __syncthreads();
+    const int fail = shifted_chol_cta(a, Z, ld, L, ld, flag, shifts, red);
+    if (!fail) {
+      inv_lower_transpose_cta(a, L, ld, Tm, ld);
+      for (int e = threadIdx.x; e < a * a; e += blockDim.x) Tm[(e % a) + (e / a) * ld] *= theta[e % a];
+      __syncthreads();
+    } else {
+      svqb_cta(a, M, ld, L, Z, ld, Tm, ld, rot, red, theta);
+    }
     // X <- X Tm, row by row (each thread owns rows of X)
     for (int r = threadIdx.x; r < s; r += blockDim.x) {
       double row[kMaxM];
@@ -357,7 +383,7 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
   __shared__ double rot[4 * (kMaxS / 2 + 1)];
   __shared__ double theta[kMaxS];
   __shared__ int conv[kMaxM];
-  __shared__ int flag, shifts, s_mconv, s_mact, s_done;
+  __shared__ int flag, shifts, s_mconv, s_mact, s_done, s_pw;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     double s2 = 0.0, mx = 0.0;
     for (int g = 0; g < nparts; ++g) {
@@ -401,28 +427,62 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
   }
   for (int e = threadIdx.x; e < s * m; e += blockDim.x) Y[(e % s) + (e / s) * ld] = U[e];
   __syncthreads();
+  // A P direction exists only where x_j moved: drop column c when (I - u_x u_x^T) u~_p_c
+  // vanishes exactly (a zero vector cannot be normalised and would give a spurious Ritz
+  // value 0 in V); pack the kept columns to the front.
+  __shared__ int keep[kMaxM];
+  for (int c = threadIdx.x; c < a; c += blockDim.x) {
+    double cf[kMaxM];
+    for (int i = 0; i < m; ++i) {
+      double d = 0.0;
+      for (int r = 0; r < s; ++r) d += Y[r + i * ld] * X[r + c * ld];
+      cf[i] = d;
+    }
+    double nrm = 0.0;
+    for (int r = 0; r < s; ++r) {
+      double v = X[r + c * ld];
+      for (int i = 0; i < m; ++i) v -= Y[r + i * ld] * cf[i];
+      nrm += v * v;
+    }
+    keep[c] = sqrt(nrm) > 1e-200 ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int kept = 0;
+    for (int c = 0; c < a; ++c)
+      if (keep[c]) {
+        if (kept != c)
+          for (int r = 0; r < s; ++r) X[r + kept * ld] = X[r + c * ld];
+        ++kept;
+      }
+    s_pw = kept;
+  }
+  __syncthreads();
+  const int ap = s_pw;
+  if (threadIdx.x == 0) state->p_cols = ap;
+  if (ap == 0) return;
   const int cap = 6, cap2 = 4;
   int passes = 0;
   for (;;) {
     // C = Y^T X, X <- X - Y C
-    for (int e = threadIdx.x; e < m * a; e += blockDim.x) {
+    for (int e = threadIdx.x; e < m * ap; e += blockDim.x) {
       const int i = e % m, j = e / m;
       double acc = 0.0;
       for (int r = 0; r < s; ++r) acc += Y[r + i * ld] * X[r + j * ld];
       C[i + j * lds] = acc;
     }
     __syncthreads();
-    for (int e = threadIdx.x; e < s * a; e += blockDim.x) {
+    for (int e = threadIdx.x; e < s * ap; e += blockDim.x) {
       const int r = e % s, j = e / s;
       double acc = 0.0;
       for (int i = 0; i < m; ++i) acc += Y[r + i * ld] * C[i + j * lds];
       X[r + j * ld] -= acc;
     }
     __syncthreads();
-    small_ortho(s, a, X, ld, tau, cap, M, L, Tm, Z, lds, rot, red, theta, &flag, &shifts);
+    small_ortho(s, ap, X, ld, tau, cap, M, L, Tm, Z, lds, rot, red, theta, &flag, &shifts);
     ++passes;
     double mx = 0.0;
-    for (int e = threadIdx.x; e < m * a; e += blockDim.x) {
+    for (int e = threadIdx.x; e < m * ap; e += blockDim.x) {
       const int i = e % m, j = e / m;
       double acc = 0.0;
       for (int r = 0; r < s; ++r) acc += Y[r + i * ld] * X[r + j * ld];
@@ -433,7 +493,33 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
     mx = block_max(mx, red);
     if (mx <= tau || passes >= cap2) break;
   }
-  for (int e = threadIdx.x; e < s * a; e += blockDim.x) up[e] = X[(e % s) + (e / s) * ld];
+  // drop columns that could not be made orthonormal against u_x (more P directions than
+  // the complement of u_x holds, e.g. after a column was unlocked); pack the rest
+  for (int c = threadIdx.x; c < ap; c += blockDim.x) {
+    double worst = 0.0, nrm = 0.0;
+    for (int i = 0; i < m; ++i) {
+      double d = 0.0;
+      for (int r = 0; r < s; ++r) d += Y[r + i * ld] * X[r + c * ld];
+      worst = fmax(worst, fabs(d));
+    }
+    for (int r = 0; r < s; ++r) nrm += X[r + c * ld] * X[r + c * ld];
+    keep[c] = (worst <= sqrt(tau) && fabs(sqrt(nrm) - 1.0) <= sqrt(tau)) ? 1 : 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int kept = 0;
+    for (int c = 0; c < ap; ++c)
+      if (keep[c]) {
+        if (kept != c)
+          for (int r = 0; r < s; ++r) X[r + kept * ld] = X[r + c * ld];
+        ++kept;
+      }
+    s_pw = kept;
+    state->p_cols = kept;
+  }
+  __syncthreads();
+  const int ap2 = s_pw;
+  for (int e = threadIdx.x; e < s * ap2; e += blockDim.x) up[e] = X[(e % s) + (e / s) * ld];
   if (threadIdx.x == 0) {
     state->sp_shifts += shifts;
     state->sp_passes = passes;
@@ -447,11 +533,12 @@ void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U
   if (s <= 0) return;
   if (s > kMaxS) throw std::invalid_argument("syev: s > 96");
   const size_t smem = (size_t)2 * s * (s + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxS * (kMaxS + 1) * 8));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   syev_kernel<<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
   LB_LAUNCH_CHECK();
 }
@@ -460,12 +547,32 @@ void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* 
   if (p <= 0) return;
   if (p > kMaxCholP) throw std::invalid_argument("cholqr: p > 64");
   const size_t smem = (size_t)4 * p * (p + 1) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(cholqr_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kMaxCholP * (kMaxCholP + 1) * 8));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   cholqr_small_kernel<<<1, kSmallThreads, smem, st>>>(p, M, tau, Linv, ctl);
+  LB_LAUNCH_CHECK();
+}
+
+namespace {
+__global__ void maxabs_minus_identity_kernel(int p, const double* __restrict__ C, double* out) {
+  __shared__ double red[32];
+  double m = 0.0;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const double v = fabs(C[e] - ((e % p) == (e / p) ? 1.0 : 0.0));
+    m = (v <= m) ? m : v;
+    if (v != v) m = INFINITY;
+  }
+  m = block_max(m, red);
+  if (threadIdx.x == 0) *out = m;
+}
+}  // namespace
+
+void launch_maxabs_minus_identity(int p, const double* C, double* out, cudaStream_t st) {
+  maxabs_minus_identity_kernel<<<1, 256, 0, st>>>(p, C, out);
   LB_LAUNCH_CHECK();
 }
 
@@ -478,11 +585,12 @@ void launch_lock_and_p(int s, int m, int k, int64_t n, const double* norm_part, 
                        const double* U, double tol, int tol_kind, double tau, LockState* state,
                        double* resnorm, double* colmax, double* up, bool build_p, cudaStream_t st) {
   const size_t smem = ((size_t)2 * kMaxM * (kMaxS + 1) + (size_t)5 * kMaxM * (kMaxM + 1)) * sizeof(double);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(lock_p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   lock_p_kernel<<<1, kSmallThreads, smem, st>>>(s, m, k, n, norm_part, nparts, U, tol, tol_kind, tau,
                                                  state, resnorm, colmax, up, build_p ? 1 : 0);
   LB_LAUNCH_CHECK();

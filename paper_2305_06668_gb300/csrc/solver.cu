@@ -78,6 +78,7 @@ struct Stats {
   int64_t spmm_launches = 0;
   int64_t spmm_launches64 = 0, spmm_columns64 = 0;
   int precond_fallback = 0;
+  int w_dropped = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -175,6 +176,7 @@ struct lobpcg_ctx {
   float cscale = 0.f;
   bool use_learned = false;  // cleared for the rest of a solve when the residuals stall
   FILE* trace = nullptr;  // per-iteration JSON lines (LOBPCG_TRACE=path)
+  bool trace_orth = false;  // LOBPCG_TRACE_ORTH=1: also trace max |V^T V - I|
 
   void sync() { LB_CUDA(cudaStreamSynchronize(st)); }
 
@@ -286,11 +288,17 @@ int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap) {
 }
 
 // Algorithm 3: W (n x p) <- ortho(W; Y), Y orthonormal (Cols).  Body runs at least once.
+// If the pass cap stops it with columns still overlapping Y by more than sqrt(tau), those
+// columns are dropped and the rest packed to the front (reading R16); *kept receives the
+// number of columns left (p otherwise).
 template <class T>
-int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double tau, int cap, int cap2) {
+int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double tau, int cap, int cap2,
+                  int* kept = nullptr) {
+  if (kept) *kept = p;
   if (p <= 0) return 0;
   const int q = Y.width();
   int passes = 0;
+  double last = 0.0;
   c.prof.mark(PH_ORTHO);
   for (;;) {
     if (q > 0) {
@@ -311,11 +319,38 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
     launch_maxabs(q * p, c.C, c.scal, c.st);
     LB_CUDA(cudaMemcpyAsync(c.host, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.st));
     c.sync();
-    if (c.host[0] <= tau) break;
+    last = c.host[0];
+    if (last <= tau) break;
     if (passes >= cap2) {
       c.stats.cap_hits++;
       break;
     }
+  }
+  if (q > 0 && kept && !(last <= std::sqrt(tau))) {
+    // R16: keep the columns whose overlap with Y is at most sqrt(tau)
+    std::vector<double> Ch((size_t)q * p);
+    LB_CUDA(cudaMemcpyAsync(Ch.data(), c.C, Ch.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    std::vector<double> sel((size_t)p * p, 0.0);  // p x p column selection (column-major)
+    int k2 = 0;
+    for (int j = 0; j < p; ++j) {
+      double worst = 0.0;
+      for (int i = 0; i < q; ++i) worst = std::max(worst, std::fabs(Ch[(size_t)j * q + i]));
+      if (worst <= std::sqrt(tau)) sel[(size_t)k2 * p + j] = 1.0, ++k2;  // W is unit after Algorithm 2
+    }
+    if (k2 < p) {
+      LB_CUDA(cudaMemcpyAsync(c.Tm, sel.data(), sel.size() * sizeof(double), cudaMemcpyHostToDevice, c.st));
+      if (k2 > 0) {
+        UpdateJob<T> job{};
+        job.in[0] = cols1<T>(W, ld, p);
+        job.out[0] = W;
+        job.ld_out[0] = ld;
+        job.nprod = 1;
+        launch_update<T>(c.A.n, job, c.Tm, p, k2, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // W <- W S
+      }
+      c.stats.w_dropped += p - k2;
+    }
+    *kept = k2;
   }
   c.stats.ortho_passes_max = std::max(c.stats.ortho_passes_max, passes);
   c.prof.mark(PH_OTHER);
@@ -356,7 +391,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   const int tol_kind = c.opt.tol_kind;
   PhaseOut out;
   int cur = 0;
-  LockState ls{0, m, 0, 0, 0};
+  LockState ls{0, m, 0, 0, 0, 0};
   LB_CUDA(cudaMemcpyAsync(c.lock, &ls, sizeof ls, cudaMemcpyHostToDevice, c.st));
 
   auto read_lock = [&](int mm) {
@@ -397,9 +432,10 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     return out;
   }
   int a = ls.m_act, m_conv = ls.m_conv;
+  int aw = a;  // columns of W (fewer than a when R16 drops some)
   precondition<T>(c, b.X[cur], b.AX[cur], ld, m_conv, a, b.W);         // W~ = T R
-  ortho_against<T>(c, b.W, ld, a, cols1<T>(b.X[cur], ld, m), tau, cap, cap2);  // W = ortho(W~; X)
-  apply_A<T>(c, b.W, ld, a, b.AW, ld);                                  // AW = A W
+  ortho_against<T>(c, b.W, ld, a, cols1<T>(b.X[cur], ld, m), tau, cap, cap2, &aw);  // W = ortho(W~; X)
+  apply_A<T>(c, b.W, ld, aw, b.AW, ld);                                 // AW = A W
   int pw = 0;  // width of P in the current basis
   double best_rk = 1e300;
   int since_best = 0;
@@ -409,13 +445,31 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   // ---- main loop ----
   int it = 1;
   for (; it <= maxiter; ++it) {
-    const int s = m + pw + a;
+    const int s = m + pw + aw;
     Cols<T> V = cols1<T>(b.X[cur], ld, m);
     V = cols_add<T>(V, b.P[cur], ld, pw);
-    V = cols_add<T>(V, b.W, ld, a);
+    V = cols_add<T>(V, b.W, ld, aw);
     Cols<T> AV = cols1<T>(b.AX[cur], ld, m);
     AV = cols_add<T>(AV, b.AP[cur], ld, pw);
-    AV = cols_add<T>(AV, b.AW, ld, a);
+    AV = cols_add<T>(AV, b.AW, ld, aw);
+    double orth_dev = -1.0;
+    int orth_i = -1, orth_j = -1;
+    if (c.trace && c.trace_orth) {
+      // optional check of the basis: max |V^T V - I| (LOBPCG_TRACE_ORTH=1)
+      gram<T>(c, V, V, false, c.G);
+      launch_maxabs_minus_identity(s, c.G, c.scal, c.st);
+      LB_CUDA(cudaMemcpyAsync(c.host + 7, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+      LB_CUDA(cudaMemcpyAsync(c.host + 64, c.G, (size_t)s * s * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+      c.sync();
+      orth_dev = c.host[7];
+      // location of the largest deviation and the column norms, for the trace
+      double worst = -1.0;
+      for (int j = 0; j < s; ++j)
+        for (int i = 0; i < s; ++i) {
+          const double d = std::fabs(c.host[64 + i + j * s] - (i == j ? 1.0 : 0.0));
+          if (d > worst) worst = d, orth_i = i, orth_j = j;
+        }
+    }
     c.prof.mark(PH_RR_GRAM);
     gram<T>(c, V, AV, true, c.G);                                       // a = V^T AV (upper)
     c.prof.mark(PH_RR_EIG);
@@ -434,8 +488,9 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     read_lock(m);
     c.prof.mark(PH_OTHER);
     if (c.trace) {
-      std::fprintf(c.trace, "{\"it\": %d, \"prec\": %d, \"s\": %d, \"sweeps\": %d, \"m_act\": %d, \"lambda\": [",
-                   it, (int)sizeof(T) * 8, s, out.sweeps, ls.m_act);
+      std::fprintf(c.trace, "{\"it\": %d, \"prec\": %d, \"s\": %d, \"pw\": %d, \"sweeps\": %d, \"m_act\": %d, "
+                   "\"orth\": %.3e, \"orth_ij\": [%d, %d], \"lambda\": [", it, (int)sizeof(T) * 8, s, pw,
+                   out.sweeps, ls.m_act, orth_dev, orth_i, orth_j);
       for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.17g", j ? ", " : "", out.lam[j]);
       std::fprintf(c.trace, "], \"res\": [");
       for (int j = 0; j < m; ++j) std::fprintf(c.trace, "%s%.6e", j ? ", " : "", out.res[j]);
@@ -475,23 +530,24 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     const int a_new = ls.m_act;
     m_conv = ls.m_conv;
     c.prof.mark(PH_UPDATE);
-    {
+    const int pw_new = ls.p_cols;  // P directions whose Ritz vector moved (reading R14)
+    if (pw_new > 0) {
       UpdateJob<T> pj{};
       pj.in[0] = V, pj.in[1] = AV;
       pj.out[0] = b.P[nxt], pj.out[1] = b.AP[nxt];
       pj.ld_out[0] = pj.ld_out[1] = ld;
       pj.nprod = 2;
-      launch_update<T>(n, pj, c.up, s, a_new, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // P = V u_p
+      launch_update<T>(n, pj, c.up, s, pw_new, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // P = V u_p
     }
     c.prof.mark(PH_OTHER);
     cur = nxt;
     a = a_new;
-    pw = a;
+    pw = pw_new;
     precondition<T>(c, b.X[cur], b.AX[cur], ld, m_conv, a, b.W);       // W~ = T R
     Cols<T> Y = cols1<T>(b.X[cur], ld, m);
-    Y = cols_add<T>(Y, b.P[cur], ld, a);
-    ortho_against<T>(c, b.W, ld, a, Y, tau, cap, cap2);                 // W = ortho(W~; (X, P))
-    apply_A<T>(c, b.W, ld, a, b.AW, ld);                                // AW = A W
+    Y = cols_add<T>(Y, b.P[cur], ld, pw);
+    ortho_against<T>(c, b.W, ld, a, Y, tau, cap, cap2, &aw);            // W = ortho(W~; (X, P))
+    apply_A<T>(c, b.W, ld, aw, b.AW, ld);                               // AW = A W
   }
   out.iterations = std::min(it, maxiter);
   out.m_conv = ls.m_conv;
@@ -648,6 +704,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     c->prof.begin(c->opt.profile != 0, c->st);
     const char* tr = std::getenv("LOBPCG_TRACE");
     c->trace = tr && *tr ? std::fopen(tr, "a") : nullptr;
+    const char* tro = std::getenv("LOBPCG_TRACE_ORTH");
+    c->trace_orth = tro && *tro == '1';
     cudaEvent_t e0, e1;
     LB_CUDA(cudaEventCreate(&e0));
     LB_CUDA(cudaEventCreate(&e1));
@@ -722,7 +780,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       job.ld_out[0] = job.ld_out[1] = b.ld;
       job.nprod = 2;
       const int parts = launch_update<double>(n, job, c->Tm, k, k, 1.0, c->lam, c->npart, c->max_ctas, c->st);
-      LockState tmp{0, k, 0, 0, 0};
+      LockState tmp{0, k, 0, 0, 0, 0};
       LB_CUDA(cudaMemcpyAsync(c->lock, &tmp, sizeof tmp, cudaMemcpyHostToDevice, c->st));
       launch_lock_and_p(k, k, k, n, c->npart, parts, c->Tm, tol, 0, tau, c->lock, c->resnorm, c->colmax, c->up, false, c->st);
     }
@@ -897,4 +955,58 @@ extern "C" lobpcg_status lobpcg_ortho_against_f64(int64_t n, int p, double* X, i
     }
     return LOBPCG_OK;
   });
+}
+
+// ============================================================ batched solve
+
+#include <atomic>
+#include <thread>
+
+extern "C" lobpcg_status lobpcg_solve_batched(lobpcg_ctx* const* ctxs, int nprob, const int* k, const double* tol,
+                                              const double* const* X0, double* const* evals, double* const* evecs,
+                                              double* const* resnorms, lobpcg_info* infos, lobpcg_status* statuses,
+                                              int nthreads) {
+  if (nprob < 0 || (nprob > 0 && (!ctxs || !k || !tol || !evals || !evecs || !resnorms || !statuses))) {
+    lobpcg::set_thread_error("lobpcg_solve_batched: NULL argument");
+    return LOBPCG_EINVAL;
+  }
+  for (int i = 0; i < nprob; ++i)
+    if (!ctxs[i]) {
+      lobpcg::set_thread_error("lobpcg_solve_batched: NULL context");
+      return LOBPCG_EINVAL;
+    }
+  if (nthreads <= 0) nthreads = 32;
+  nthreads = std::min(nthreads, std::max(nprob, 1));
+  // larger problems first: the longest solves start early and the tail stays short
+  std::vector<int> order(nprob);
+  for (int i = 0; i < nprob; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int a, int b) {
+    const double wa = (double)ctxs[a]->A.n * (k[a] + ctxs[a]->opt.extra);
+    const double wb = (double)ctxs[b]->A.n * (k[b] + ctxs[b]->opt.extra);
+    return wa > wb;
+  });
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int t = next.fetch_add(1);
+      if (t >= nprob) break;
+      const int i = order[t];
+      statuses[i] = lobpcg_solve(ctxs[i], k[i], tol[i], X0 ? X0[i] : nullptr, evals[i], evecs[i], resnorms[i],
+                                 infos ? &infos[i] : nullptr);
+      // only the problems in flight hold block workspace: a finished problem returns its own
+      ctxs[i]->b64.buf.release();
+      ctxs[i]->b32.buf.release();
+      ctxs[i]->x0buf.release();
+    }
+  };
+  std::vector<std::thread> pool;
+  pool.reserve(nthreads);
+  for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+  for (auto& th : pool) th.join();
+  for (int i = 0; i < nprob; ++i)
+    if (statuses[i] != LOBPCG_OK) return statuses[i];
+  return LOBPCG_OK;
 }

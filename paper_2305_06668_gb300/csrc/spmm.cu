@@ -394,12 +394,13 @@ bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   const size_t smem = (size_t)win * row_bytes + csr_bytes;
   if (smem > 220 * 1024) return false;
   constexpr int UNR = (L < 4 ? L : 4);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(spmm_csr_band_kernel<T, V, L, UNR, RS, NV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  225 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   const int64_t ctas = ceil_div(n, R);
   spmm_csr_band_kernel<T, V, L, UNR, RS, NV><<<(unsigned)ctas, 512, smem, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy,
                                                                               (int)R, band, pp, cap);

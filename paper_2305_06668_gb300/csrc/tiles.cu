@@ -406,12 +406,13 @@ int update_row_launch(int64_t n, const UpdateJob<T>& job, int ld, const double* 
                       const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
   const int threads = 256;
   const size_t smem = std::max((size_t)s * QMAX * sizeof(T), (size_t)(threads / 32) * 2 * QMAX * sizeof(double));
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(update_row_kernel<T, QMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  64 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, threads));
   if (ctas < 1) ctas = 1;
   const int64_t rpc = ceil_div(n, ctas);
@@ -448,12 +449,13 @@ int gram_pipe_launch(int64_t n, const Cols<T>& a, const Cols<T>& b, int ld, bool
   const size_t ring = (size_t)S * (a.nseg + b.nseg) * R * lds * sizeof(T);
   const size_t red = (size_t)ntiles * TI * TJ * sizeof(double);
   const size_t smem = std::max(ring, red);
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(gram_pipe_kernel<T, TI, TJ, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
   if (ctas < 1) ctas = 1;
   const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
@@ -510,12 +512,13 @@ int launch_update_pipe(int64_t n, const UpdateJob<T>& job, const double* U, int 
   const size_t red = norm_part ? (size_t)(R / RJ) * 2 * qpad * sizeof(double) : 0;
   const size_t smem = head + std::max(ring, red) + 16;
   if (smem > 200 * 1024) return 0;
-  static bool attr = false;
-  if (!attr) {
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
     LB_CUDA(cudaFuncSetAttribute(update_pipe_kernel<T, RJ, CJ, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  200 * 1024));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
   if (ctas < 1) ctas = 1;
   const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;

@@ -176,3 +176,60 @@ def random_sparse_sym(n: int, per_row: int, seed: int, diag_scale: float = 1.0,
 
 def dense_from_csr(a: CSR) -> np.ndarray:
     return np.asfortranarray(a.to_scipy().toarray())
+
+
+def sparse_cfg1_torch(n: int, seed: int, device="cuda", per_row: int = 16, sigma: float = 0.01,
+                      step: float = 0.01, jitter: float = 0.005):
+    """The cfg1 recipe generated on the GPU with torch's seeded Philox generator.
+
+    Same construction as sparse_cfg1 (diagonal step*i + U(0, jitter) sorted, per_row random
+    couplings j != i per row, unordered pairs deduplicated keeping the first, mirrored,
+    N(0, sigma^2)), for the large batched workload where host generation would take
+    minutes.  Returns CUDA tensors (row_ptr int64, col_idx int32, val float64, diag float64).
+    The random stream differs from the numpy one, so the matrices differ from sparse_cfg1.
+    """
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    ar = torch.arange(n, device=device, dtype=torch.int64)
+    diag = torch.sort(step * ar.double() + jitter * torch.rand(n, generator=g, device=device, dtype=torch.float64)).values
+    i = ar.repeat_interleave(per_row)
+    r = torch.randint(0, n - 1, (n * per_row,), generator=g, device=device, dtype=torch.int64)
+    j = torch.where(r >= i, r + 1, r)
+    v = sigma * torch.randn(n * per_row, generator=g, device=device, dtype=torch.float64)
+    lo, hi = torch.minimum(i, j), torch.maximum(i, j)
+    key = lo * n + hi
+    # first occurrence of every key in generation order
+    sk, perm = torch.sort(key, stable=True)
+    first = torch.ones_like(sk, dtype=torch.bool)
+    first[1:] = sk[1:] != sk[:-1]
+    keep = perm[first]
+    keep, _ = torch.sort(keep)
+    lo, hi, v = lo[keep], hi[keep], v[keep]
+    rows = torch.cat([lo, hi, ar])
+    cols = torch.cat([hi, lo, ar])
+    vals = torch.cat([v, v, diag])
+    order = torch.argsort(rows * n + cols)
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = torch.bincount(rows, minlength=n)
+    row_ptr = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    row_ptr[1:] = torch.cumsum(counts, 0)
+    return dict(row_ptr=row_ptr, col_idx=cols.to(torch.int32).contiguous(), val=vals.contiguous(), diag=diag)
+
+
+def batched_specs(nprob: int = 256, seed: int = 0, n_range=(10_000, 500_000), k_range=(1, 32)):
+    """(n, k, seed) of the batched serving workload: n ~ U[n_range], k ~ U{k_range}."""
+    g = rng(seed, 7)
+    ns = g.integers(n_range[0], n_range[1] + 1, size=nprob)
+    ks = g.integers(k_range[0], k_range[1] + 1, size=nprob)
+    return [(int(n), int(k), int(seed) * 100_000 + p) for p, (n, k) in enumerate(zip(ns, ks))]
+
+
+def diag_guess_torch(diag, m: int):
+    """Unit vectors at the m smallest diagonal entries (n x m float64 on diag's device)."""
+    import torch
+    n = diag.numel()
+    idx = torch.argsort(diag, stable=True)[:m]
+    x = torch.zeros((n, m), dtype=torch.float64, device=diag.device)
+    x[idx, torch.arange(m, device=diag.device)] = 1.0
+    return x
