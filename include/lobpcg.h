@@ -99,7 +99,9 @@ typedef struct {
                                  (LOBPCG_PREC_LEARNED); copied by lobpcg_create */
   int profile;                /* non-zero: fill lobpcg_info.phase_seconds (adds CUDA events) */
   double mixed_switch;        /* MIXED: leave FP32 once the k sought residuals are <= this;
-                                 0 (default) = when the largest stops improving */
+                                 0 (default) = when the largest stops improving: no 10% drop
+                                 in 2 iterations once it is below 1% of its first value, or
+                                 in 5 iterations at any level */
 } lobpcg_options;
 
 typedef struct {
@@ -184,6 +186,19 @@ LOBPCG_API const char* lobpcg_last_error(const lobpcg_ctx* ctx);
 LOBPCG_API lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                                   const double* val, int p, const double* X, int ldx, double* Y,
                                   int ldy, lobpcg_stream stream);
+
+/* Y = A X in FP32 with A's values rounded to FP32: the product of the mixed form
+ * (Algorithm 1, "AW = A W", with FP32 blocks).  X, Y: n x p float, row-major, 16-byte
+ * aligned with ldx, ldy multiples of 4; p <= 32.  band = -1 picks the half-width b that
+ * holds 80% of the entries (the choice lobpcg_create makes); band >= 0 forces b; band = -2
+ * uses the unsplit product.  With b >= 0 the matrix is split into A_band (|col - row| <= b,
+ * gathered from a shared-memory window of X) and A_lr (the rest, added by a second
+ * kernel).  *band_used (nullable) receives b, or -1 for the unsplit product.  Allocates
+ * its temporaries (the split copy of A) on every call.  EINVAL for bad sizes, NULL
+ * pointers or misaligned blocks. */
+LOBPCG_API lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                  const double* val, int64_t nnz, int p, const float* X, int ldx,
+                                  float* Y, int ldy, int band, int* band_used, lobpcg_stream stream);
 
 /* Y = A X for dense column-major symmetric A (lda >= n); X, Y as above, p <= 32. */
 LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64_t lda, int p,

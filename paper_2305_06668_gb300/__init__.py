@@ -69,7 +69,8 @@ def lib():
                      "lobpcg_spmm_dense_f64", "lobpcg_gram_f64", "lobpcg_syev_f64", "lobpcg_ortho_f64",
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
-                     "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched"):
+                     "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
+                     "lobpcg_spmm_csr_f32"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -218,6 +219,22 @@ def spmm_csr(row_ptr, col_idx, val, X, stream=None):
     _check(lib().lobpcg_spmm_csr_f64(C.c_int64(n), _ptr(row_ptr), _ptr(col_idx), _ptr(val), C.c_int(p),
                                      _ptr(X), C.c_int(X.stride(0)), _ptr(Y), C.c_int(Y.stride(0)), _stream(stream)))
     return Y
+
+
+def spmm_csr_f32(row_ptr, col_idx, val, X, band=-1, stream=None):
+    """FP32 product of the mixed form: Y = fp32(A) X for a float32 row-major block X whose
+    leading dimension is a multiple of 4 (pad the columns if needed).  band: -1 automatic
+    band / long-range split, >= 0 forced half-width, -2 unsplit.  Returns (Y, band used)."""
+    torch = _torch()
+    n, p = X.shape
+    if X.dtype != torch.float32:
+        raise TypeError("spmm_csr_f32: X must be float32")
+    Y = torch.empty((n, X.stride(0)), dtype=X.dtype, device=X.device)[:, :p]
+    used = C.c_int(0)
+    _check(lib().lobpcg_spmm_csr_f32(C.c_int64(n), _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                     C.c_int64(val.numel()), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), _ptr(Y),
+                                     C.c_int(Y.stride(0)), C.c_int(band), C.byref(used), _stream(stream)))
+    return Y, used.value
 
 
 def spmm_dense(A, X, stream=None):

@@ -86,10 +86,28 @@ __device__ __forceinline__ T warp_max(T v) {
 
 // Y = A X, CSR, row-major blocks.  p <= 32.  band >= 0: half-width of the band that holds
 // most non-zeros (from profile_band); the product then stages that window of X in
-// shared memory.
+// shared memory.  pure: every entry satisfies |col - row| <= band (the band part of a
+// split matrix), so no gather leaves the window.
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val,
-                     int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band = -1);
+                     int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band = -1,
+                     bool pure = false);
+// Y += A X for a CSR matrix whose rows hold few, scattered entries (the long-range part of
+// a band / long-range split).  Row-major 16-byte aligned blocks, p <= 32.
+template <class T, class V>
+void launch_spmm_csr_add(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val, int p,
+                         const T* X, int ldx, T* Y, int ldy, cudaStream_t st);
+// Band / long-range split A = A_band + A_lr with A_band holding |col - row| <= band:
+// per-row counts, exclusive scan of counts into row pointers (scratch: split_scan_scratch(n)
+// int64), and the scatter of column indices and values (rounded to V).
+void split_csr_count(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int band, int32_t* cnt_band,
+                     int32_t* cnt_lr, cudaStream_t st);
+int64_t split_scan_scratch(int64_t n);
+void split_csr_rowptr(int64_t n, const int32_t* cnt, int64_t* row_ptr_out, int64_t* scratch, cudaStream_t st);
+template <class V>
+void split_csr_scatter(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int band,
+                       const int64_t* rp_band, int32_t* ci_band, V* v_band, const int64_t* rp_lr, int32_t* ci_lr,
+                       V* v_lr, cudaStream_t st);
 // Smallest half-width b in {16, ..., 2048} with 80% of the non-zeros at |col - row| <= b,
 // or -1 (synchronises the stream).
 int profile_band(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, cudaStream_t st);

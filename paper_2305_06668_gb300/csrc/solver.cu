@@ -17,6 +17,7 @@
 #include <cstring>
 #include <memory>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/lobpcg.h"
@@ -149,6 +150,61 @@ struct Blocks {
 
 }  // namespace
 
+// FP32 copy of a CSR matrix split into A_band (|col - row| <= band) and A_lr (the rest),
+// both in CSR with the original row order of the entries.
+struct SplitCSR {
+  DevBuf rp_buf, ci_buf, val_buf;
+  const int64_t *rp_band = nullptr, *rp_lr = nullptr;
+  const int32_t *ci_band = nullptr, *ci_lr = nullptr;
+  const float *v_band = nullptr, *v_lr = nullptr;
+  int64_t nnz_band = 0, nnz_lr = 0;
+  int band = -1;
+
+  void build(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int64_t nnz, int b,
+             cudaStream_t st) {
+    DevBuf cnt, scratch;
+    cnt.ensure((size_t)2 * std::max<int64_t>(n, 1) * sizeof(int32_t));
+    scratch.ensure((size_t)split_scan_scratch(n) * sizeof(int64_t));
+    int32_t* cb = cnt.as<int32_t>();
+    int32_t* cl = cb + n;
+    split_csr_count(n, row_ptr, col_idx, b, cb, cl, st);
+    rp_buf.ensure((size_t)2 * (n + 1) * sizeof(int64_t));
+    int64_t* rpb = rp_buf.as<int64_t>();
+    int64_t* rpl = rpb + (n + 1);
+    split_csr_rowptr(n, cb, rpb, scratch.as<int64_t>(), st);
+    split_csr_rowptr(n, cl, rpl, scratch.as<int64_t>(), st);
+    int64_t tot[2] = {0, 0};
+    LB_CUDA(cudaMemcpyAsync(&tot[0], rpb + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaMemcpyAsync(&tot[1], rpl + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaStreamSynchronize(st));
+    if (tot[0] + tot[1] != nnz) throw std::runtime_error("band split: entry counts do not add up to nnz");
+    nnz_band = tot[0], nnz_lr = tot[1];
+    const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
+    ci_buf.ensure(nz * sizeof(int32_t));
+    val_buf.ensure(nz * sizeof(float));
+    int32_t* cib = ci_buf.as<int32_t>();
+    float* vb = val_buf.as<float>();
+    split_csr_scatter<float>(n, row_ptr, col_idx, val, b, rpb, cib, vb, rpl, cib + tot[0], vb + tot[0], st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    cnt.release();
+    scratch.release();
+    rp_band = rpb, rp_lr = rpl;
+    ci_band = cib, ci_lr = cib + tot[0];
+    v_band = vb, v_lr = vb + tot[0];
+    band = b;
+  }
+  // Y = A_band X, then Y += A_lr X
+  void apply(int64_t n, int p, const float* X, int ldx, float* Y, int ldy, cudaStream_t st) const {
+    launch_spmm_csr<float, float>(n, rp_band, ci_band, v_band, p, X, ldx, Y, ldy, st, band, true);
+    if (nnz_lr > 0) launch_spmm_csr_add<float, float>(n, rp_lr, ci_lr, v_lr, p, X, ldx, Y, ldy, st);
+  }
+  void release() {
+    rp_buf.release();
+    ci_buf.release();
+    val_buf.release();
+  }
+};
+
 struct lobpcg_ctx {
   lobpcg_matrix A{};
   lobpcg_options opt{};
@@ -159,6 +215,10 @@ struct lobpcg_ctx {
   int band = -1;  // CSR: half-width holding most non-zeros (shared-memory window of the product)
 
   DevBuf val32, dense32;  // FP32 copies for the mixed form
+  // mixed form, CSR with a band: the FP32 matrix split into the band part (|col - row| <=
+  // band, product from a shared-memory window of X) and the long-range rest
+  SplitCSR sp;
+  bool split = false;
   Blocks<double> b64;
   Blocks<float> b32;
   DevBuf small;  // all small FP64 matrices and partials
@@ -231,7 +291,9 @@ template <class T>
 void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
   if (p <= 0) return;
   c.prof.mark(PH_SPMM);
-  if (c.A.fmt == LOBPCG_CSR)
+  if (c.A.fmt == LOBPCG_CSR && std::is_same<T, float>::value && c.split)
+    c.sp.apply(c.A.n, p, reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy, c.st);
+  else if (c.A.fmt == LOBPCG_CSR)
     launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st, c.band);
   else
     launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
@@ -437,7 +499,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   ortho_against<T>(c, b.W, ld, a, cols1<T>(b.X[cur], ld, m), tau, cap, cap2, &aw);  // W = ortho(W~; X)
   apply_A<T>(c, b.W, ld, aw, b.AW, ld);                                 // AW = A W
   int pw = 0;  // width of P in the current basis
-  double best_rk = 1e300;
+  double best_rk = 1e300, first_rk = -1.0;
   int since_best = 0;
   double lbest = 1e300;
   int lsince = 0;
@@ -504,9 +566,11 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     if (stall_exit) {
       // mixed-precision switch: leave this precision once every one of the k sought
       // residuals is below switch_tol, or (switch_tol == 0) once the largest of them has
-      // not improved by 10% for 5 iterations (its rounding floor)
+      // reached its rounding floor: no 10% improvement for 2 iterations after it fell
+      // below 1% of its first value, or for 5 iterations at any level
       double rk = 0.0;
       for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
+      if (first_rk < 0.0) first_rk = rk;
       if (switch_tol > 0.0) {
         if (rk <= switch_tol) {
           cur = nxt;
@@ -514,7 +578,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
         }
       } else if (rk < 0.9 * best_rk) {
         best_rk = rk, since_best = 0;
-      } else if (++since_best >= 5) {
+      } else if (++since_best >= 5 || (since_best >= 2 && best_rk <= 1e-2 * first_rk)) {
         cur = nxt;
         break;
       }
@@ -658,7 +722,10 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
     require(finite == 1, "lobpcg_create: matrix or diagonal has non-finite entries");
     if (A->fmt == LOBPCG_CSR) c->band = profile_band(A->n, A->row_ptr, A->col_idx, A->nnz, c->st);
     if (c->opt.precision == LOBPCG_MIXED) {
-      if (A->fmt == LOBPCG_CSR) {
+      if (A->fmt == LOBPCG_CSR && c->band >= 0) {
+        c->sp.build(A->n, A->row_ptr, A->col_idx, A->val, A->nnz, c->band, c->st);
+        c->split = true;
+      } else if (A->fmt == LOBPCG_CSR) {
         c->val32.ensure((size_t)std::max<int64_t>(A->nnz, 1) * sizeof(float));
         launch_to_float(A->nnz, A->val, c->val32.as<float>(), c->st);
       } else {
@@ -828,6 +895,7 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   cudaStreamSynchronize(c->st);
   c->val32.release();
   c->dense32.release();
+  c->sp.release();
   c->b64.buf.release();
   c->b32.buf.release();
   c->small.release();
@@ -876,6 +944,38 @@ extern "C" lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, 
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     launch_spmm_csr<double, double>(n, row_ptr, col_idx, val, p, X, ldx, Y, ldy, st);
     LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                             const double* val, int64_t nnz, int p, const float* X, int ldx,
+                                             float* Y, int ldy, int band, int* band_used, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 0 && nnz >= 0 && row_ptr && col_idx && val && X && Y, "lobpcg_spmm_csr_f32: NULL argument");
+    require(p >= 1 && p <= 32 && ldx >= p && ldy >= p, "lobpcg_spmm_csr_f32: need 1 <= p <= 32, ld >= p");
+    require(ldx % 4 == 0 && ldy % 4 == 0 && !(reinterpret_cast<uintptr_t>(X) & 15) &&
+                !(reinterpret_cast<uintptr_t>(Y) & 15),
+            "lobpcg_spmm_csr_f32: X and Y must be 16-byte aligned with ld a multiple of 4");
+    require(band >= -2, "lobpcg_spmm_csr_f32: band must be -2, -1 or >= 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    int b = band;
+    if (b == -1) b = profile_band(n, row_ptr, col_idx, nnz, st);
+    if (b >= 0) {
+      SplitCSR sp;
+      sp.build(n, row_ptr, col_idx, val, nnz, b, st);
+      sp.apply(n, p, X, ldx, Y, ldy, st);
+      LB_CUDA(cudaStreamSynchronize(st));
+      sp.release();
+    } else {
+      DevBuf v32;
+      v32.ensure((size_t)std::max<int64_t>(nnz, 1) * sizeof(float));
+      launch_to_float(nnz, val, v32.as<float>(), st);
+      launch_spmm_csr<float, float>(n, row_ptr, col_idx, v32.as<float>(), p, X, ldx, Y, ldy, st);
+      LB_CUDA(cudaStreamSynchronize(st));
+      v32.release();
+    }
+    if (band_used) *band_used = b < 0 ? -1 : b;
     return LOBPCG_OK;
   });
 }

@@ -9,6 +9,8 @@
 // Dense: a warp owns RB rows of the symmetric column-major A (row i == column i, so a
 // row is contiguous); lanes stride over the columns with coalesced loads of A and keep
 // RB x PC partial sums, reduced by warp shuffles.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace lobpcg {
@@ -244,6 +246,56 @@ __device__ __forceinline__ void stage_csr(const int32_t* __restrict__ ci, const 
   }
 }
 
+__device__ __forceinline__ void cp_async8_sp(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+}
+
+// Sum of a lane's V values over the G = 32/L lane groups of a warp, left scattered over
+// the lanes (a transpose reduction): at each xor level a lane keeps half of its values
+// (the upper half when its level bit is set) and adds the partner's copy of that half, so
+// the levels exchange V/2 + V/4 + ... values instead of V each.  On return the lane holds
+// in acc[0 .. Scatter<L, V>::keep) the sums of its chunk's values [off, off + keep);
+// `owner` is false on the lanes that hold a duplicate (levels after the count turned odd).
+template <int L, int V>
+struct Scatter {
+  static constexpr int kept() {
+    int cur = V;
+    for (int o = L; o < kWarp; o <<= 1)
+      if (cur > 1 && (cur & 1) == 0) cur >>= 1;
+    return cur;
+  }
+  static constexpr int keep = kept();
+};
+template <int L, int V, class T>
+__device__ __forceinline__ int reduce_scatter(T (&acc)[V], int lane, bool& owner) {
+  int off = 0;
+  owner = true;
+#pragma unroll
+  for (int o = L, cur = V; o < kWarp; o <<= 1) {
+    const bool up = (lane & o) != 0;
+    if (cur > 1 && (cur & 1) == 0) {
+      const int half = cur >> 1;
+#pragma unroll
+      for (int i = 0; i < V / 2; ++i)
+        if (i < half) {
+          const T send = up ? acc[i] : acc[i + half];
+          const T keep = up ? acc[i + half] : acc[i];
+          acc[i] = keep + __shfl_xor_sync(0xffffffffu, send, o);
+        }
+      if (up) off += half;
+      cur = half;
+    } else {
+      // odd count: plain butterfly on what is left; the upper lane becomes a duplicate
+#pragma unroll
+      for (int i = 0; i < V; ++i)
+        if (i < cur) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+      if (up) owner = false;
+    }
+  }
+  return off;
+}
+
 // The CTA owns rows [r0, r0 + R).  It copies rows [r0 - band, r0 + R + band) of X into
 // shared memory, then walks its rows in sub-blocks of RS rows whose (col, val) streams are
 // double-buffered in shared memory with cp.async, so the HBM stream of the matrix stays
@@ -408,6 +460,358 @@ bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   return true;
 }
 
+// Band part of a split matrix (every entry has |col - row| <= band), FP32.  The CTA owns
+// rows [r0, r0 + R) and keeps rows [r0 - band, r0 + R + band) of X in shared memory (row
+// stride pp = p rounded up to 16 bytes), plus one zero row that the lanes past the end
+// of a row read instead of masking their data.  The matrix streams through in sub-blocks
+// of RS rows: row pointers and interleaved (column, value) pairs are double-buffered in
+// shared memory with cp.async one sub-block ahead.  A group of L lanes takes one
+// non-zero and reads its row of X as L consecutive 16-byte vectors, so each quarter-warp
+// phase of a gather reads one contiguous row (free of bank conflicts); G = 32/L non-zeros
+// per warp step, UNR steps in flight, and a transpose reduction over the G groups.
+template <class T, class V, int L, int UNR, int RS>
+__global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                                              const int32_t* __restrict__ ci,
+                                                              const V* __restrict__ val, int p,
+                                                              const T* __restrict__ X, int ldx,
+                                                              T* __restrict__ Y, int ldy, int R, int band,
+                                                              int pp, int cap) {
+  static_assert(sizeof(V) == 4, "interleaved staging holds 4-byte values");
+  using VT = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int G = kWarp / L;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r_end = min(n, r0 + R);
+  const int64_t lo = max((int64_t)0, r0 - band), hi = min(n, r_end + band);
+  const int win = (int)(hi - lo);
+  const int nvec = pp / VEC;
+  T* tile = reinterpret_cast<T*>(smem_raw);                                                 // [win + 1][pp]
+  int64_t* srp = reinterpret_cast<int64_t*>(smem_raw + (size_t)(win + 1) * pp * sizeof(T));  // [2][RS + 1]
+  int2* scv = reinterpret_cast<int2*>(srp + 2 * (RS + 1));                                // [2][cap] (col, val bits)
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x / kWarp, wpc = blockDim.x / kWarp;
+  for (int e = threadIdx.x; e < win * nvec; e += blockDim.x) {
+    const int rr = e / nvec, w = e - rr * nvec;
+    cp_async16_sp(tile + (int64_t)rr * pp + w * VEC, X + (lo + rr) * ldx + w * VEC);
+  }
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) tile[(int64_t)win * pp + e] = T(0);
+  const int nsub = (int)((r_end - r0 + RS - 1) / RS);
+  auto bounds = [&](int k, int64_t& eb, int64_t& ee) {
+    const int64_t a = r0 + (int64_t)k * RS, b = min(r_end, a + RS);
+    eb = rp[a];
+    ee = rp[b];
+  };
+  auto stage = [&](int k, int buf, int64_t eb, int64_t ee) {
+    const int64_t a = r0 + (int64_t)k * RS;
+    const int rows = (int)(min(r_end, a + RS) - a);
+    for (int i = threadIdx.x; i <= rows; i += blockDim.x) cp_async8_sp(srp + buf * (RS + 1) + i, rp + a + i);
+    if (ee - eb <= cap) {
+      int2* d = scv + buf * cap;
+      for (int i = threadIdx.x; i < (int)(ee - eb); i += blockDim.x) {
+        cp_async4_sp(&d[i].x, ci + eb + i);
+        cp_async4_sp(&d[i].y, val + eb + i);
+      }
+    }
+  };
+  int64_t eb, ee, nb = 0, ne = 0;
+  bounds(0, eb, ee);
+  stage(0, 0, eb, ee);
+  asm volatile("cp.async.commit_group;\n" ::);
+  if (nsub > 1) bounds(1, nb, ne);
+  const int g = lane / L, li = lane % L;
+  const bool has_vec = li < nvec;
+  const T* tile_l = tile + li * VEC;
+  const int ilo = (int)lo;
+  for (int k = 0; k < nsub; ++k) {
+    const int buf = k & 1;
+    if (k + 1 < nsub) stage(k + 1, buf ^ 1, nb, ne);  // buffer buf^1 was last read in k - 1
+    asm volatile("cp.async.commit_group;\n" ::);
+    int64_t fb = 0, fe = 0;
+    if (k + 2 < nsub) bounds(k + 2, fb, fe);  // in flight during this sub-block
+    asm volatile("cp.async.wait_group 1;\n" ::);
+    __syncthreads();
+    const bool staged = ee - eb <= cap;
+    const int2* sp = scv + buf * cap;
+    const int64_t* brp = srp + buf * (RS + 1);
+    const int64_t rb = r0 + (int64_t)k * RS;
+    const int rows = (int)(min(r_end, rb + RS) - rb);
+    for (int r = wid; r < rows; r += wpc) {
+      const int le0 = (int)(brp[r] - eb), le1 = (int)(brp[r + 1] - eb);
+      T acc[VEC];
+#pragma unroll
+      for (int t = 0; t < VEC; ++t) acc[t] = T(0);
+      for (int lj = le0; lj < le1; lj += G * UNR) {
+        VT xv[UNR];
+        T vv[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+          const int le = lj + u * G + g;
+          int c = ilo - 1;  // no entry: the zero row
+          T v = T(0);
+          if (le < le1) {
+            if (staged) {
+              const int2 cv = sp[le];
+              c = cv.x, v = (T)__int_as_float(cv.y);
+            } else {
+              c = ci[eb + le], v = (T)val[eb + le];
+            }
+          }
+          vv[u] = v;
+          // in the window by construction (the clamp keeps a malformed index in bounds)
+          const unsigned o = min((unsigned)(c - ilo), (unsigned)win);
+          xv[u] = *reinterpret_cast<const VT*>(tile_l + (int)o * pp);
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) vfma(vv[u], xv[u], acc);
+      }
+      bool owner;
+      const int off = reduce_scatter<L, VEC>(acc, lane, owner);
+      if (owner && has_vec) {
+        T* yr = Y + (rb + r) * ldy + li * VEC + off;
+#pragma unroll
+        for (int t = 0; t < Scatter<L, VEC>::keep; ++t)
+          if (li * VEC + off + t < p) yr[t] = acc[t];
+      }
+    }
+    eb = nb, ee = ne, nb = fb, ne = fe;
+    __syncthreads();  // buffer `buf` is refilled in the next iteration's prefetch
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <class T, class V, int L>
+bool csr_window_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
+                       T* Y, int ldy, int band, cudaStream_t st) {
+  constexpr int VEC = 16 / sizeof(T);
+  constexpr int RS = 64;
+  constexpr int UNR = L;  // G * UNR = 32 non-zeros per batch
+  const int pp = round_up(p, VEC);
+  if (ldx < pp || pp > L * VEC) return false;
+  const size_t row_bytes = (size_t)pp * sizeof(T);
+  const int cap = 4096;  // non-zeros per staged sub-block of RS rows
+  const size_t fixed = (size_t)2 * cap * sizeof(int2) + (size_t)2 * (RS + 1) * sizeof(int64_t);
+  const size_t budget = 216 * 1024;
+  if (budget <= fixed + row_bytes) return false;
+  // rows per CTA: as many as fit beside the two band halos and the zero row
+  int64_t R = (int64_t)((budget - fixed) / row_bytes) - 1 - 2 * (int64_t)band;
+  R = R / RS * RS;
+  if (R < RS) return false;
+  R = std::min<int64_t>(R, std::max<int64_t>(RS, ceil_div(ceil_div(n, 152), RS) * RS));
+  const int64_t win = std::min<int64_t>(n, R + 2 * (int64_t)band);
+  const size_t smem = (size_t)(win + 1) * row_bytes + fixed;
+  if (smem > 220 * 1024) return false;
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(spmm_csr_window_kernel<T, V, L, UNR, RS>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 225 * 1024));
+    return true;
+  }();
+  (void)attr;
+  const int64_t ctas = ceil_div(n, R);
+  spmm_csr_window_kernel<T, V, L, UNR, RS><<<(unsigned)ctas, 512, smem, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy,
+                                                                            (int)R, band, pp, cap);
+  LB_LAUNCH_CHECK();
+  return true;
+}
+
+// Long-range part of a split product: Y += A_lr X.  A_lr holds the few couplings per row
+// that lie outside the band, so the rows of X it reads are scattered over the whole
+// block.  Each group of L lanes owns one row of Y (NV 16-byte vectors per lane, no
+// cross-lane reduction) and walks that row's entries UNR at a time, issuing all UNR
+// gathers before using them; a warp thus keeps G = 32/L rows x UNR gathers in flight.
+template <class T, class V, int L, int NV, int UNR>
+__global__ void __launch_bounds__(256) spmm_csr_add_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                                           const int32_t* __restrict__ ci,
+                                                           const V* __restrict__ val, int p,
+                                                           const T* __restrict__ X, int ldx,
+                                                           T* __restrict__ Y, int ldy) {
+  using VT = typename Vec16<T>::type;
+  constexpr int VEC = Vec16<T>::n;
+  constexpr int G = kWarp / L;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / L, li = lane % L;
+  const int col0 = li * VEC * NV;
+  const bool has_cols = col0 < p;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kWarp) * G;
+  for (int64_t row = ((int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * G + g; row < n;
+       row += groups) {
+    const int64_t e0 = rp[row], e1 = rp[row + 1];
+    if (e0 == e1 || !has_cols) continue;
+    T acc[NV][VEC];
+#pragma unroll
+    for (int w = 0; w < NV; ++w)
+#pragma unroll
+      for (int t = 0; t < VEC; ++t) acc[w][t] = T(0);
+    for (int64_t e = e0; e < e1; e += UNR) {
+      VT xv[UNR][NV];
+      T vv[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const bool valid = e + u < e1;
+        const int c = valid ? ci[e + u] : 0;
+        vv[u] = valid ? (T)val[e + u] : T(0);
+        const VT* src = reinterpret_cast<const VT*>(X + (int64_t)c * ldx + col0);
+#pragma unroll
+        for (int w = 0; w < NV; ++w) xv[u][w] = (valid && col0 + w * VEC < p) ? __ldg(src + w) : VT{};
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int w = 0; w < NV; ++w) vfma(vv[u], xv[u][w], acc[w]);
+    }
+    T* yr = Y + row * ldy + col0;
+#pragma unroll
+    for (int w = 0; w < NV; ++w) {
+      const int cw = col0 + w * VEC;
+      if (cw + VEC <= p) {
+        VT y = *reinterpret_cast<const VT*>(yr + w * VEC);
+        T* py = reinterpret_cast<T*>(&y);
+#pragma unroll
+        for (int t = 0; t < VEC; ++t) py[t] += acc[w][t];
+        *reinterpret_cast<VT*>(yr + w * VEC) = y;
+      } else {
+#pragma unroll
+        for (int t = 0; t < VEC; ++t)
+          if (cw + t < p) yr[w * VEC + t] += acc[w][t];
+      }
+    }
+  }
+}
+
+template <class T, class V, int L, int NV>
+void csr_add_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
+                    T* Y, int ldy, cudaStream_t st) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256;
+  constexpr int G = kWarp / L;
+  int64_t ctas = std::min<int64_t>(ceil_div(n, (threads / kWarp) * G), (int64_t)sms * 6);
+  if (ctas < 1) ctas = 1;
+  spmm_csr_add_kernel<T, V, L, NV, 4><<<(unsigned)ctas, threads, 0, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy);
+  LB_LAUNCH_CHECK();
+}
+
+// ---- band / long-range split of a CSR matrix (once, when the solver is created) ----
+
+// Per row: number of entries with |col - row| <= band (cb) and the rest (cl).
+__global__ void split_count_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                   int band, int32_t* __restrict__ cb, int32_t* __restrict__ cl) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    int b = 0, l = 0;
+    for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+      const int64_t d = ci[e] > row ? ci[e] - row : row - ci[e];
+      if (d <= band) ++b;
+      else ++l;
+    }
+    cb[row] = b;
+    cl[row] = l;
+  }
+}
+
+// Exclusive prefix sum of n int32 counts into n + 1 int64 row pointers, in three passes:
+// per-tile sums, one CTA scanning the tile sums, per-tile rescan with the tile offset.
+constexpr int kScanThreads = 256, kScanPer = 16, kScanTile = kScanThreads * kScanPer;
+
+__global__ void __launch_bounds__(kScanThreads) scan_tile_sums_kernel(int64_t n, const int32_t* __restrict__ cnt,
+                                                                      int64_t* __restrict__ tsum) {
+  __shared__ int64_t red[kScanThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  int64_t s = 0;
+  for (int i = threadIdx.x; i < kScanTile; i += kScanThreads) {
+    const int64_t j = base + i;
+    if (j < n) s += cnt[j];
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x / kWarp] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t t = 0;
+    for (int w = 0; w < kScanThreads / kWarp; ++w) t += red[w];
+    tsum[blockIdx.x] = t;
+  }
+}
+
+// In-place exclusive scan of the tile sums by one CTA of 1024 threads, 1024 at a time.
+__global__ void __launch_bounds__(1024) scan_tile_offsets_kernel(int64_t ntiles, int64_t* __restrict__ tsum) {
+  __shared__ int64_t wsum[32];
+  __shared__ int64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x / kWarp;
+  for (int64_t base = 0; base < ntiles; base += 1024) {
+    const int64_t j = base + threadIdx.x;
+    const int64_t v = j < ntiles ? tsum[j] : 0;
+    int64_t x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[w] = x;
+    __syncthreads();
+    int64_t wo = 0;
+    for (int i = 0; i < w; ++i) wo += wsum[i];
+    const int64_t c = carry;
+    if (j < ntiles) tsum[j] = c + wo + x - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = c + wo + x;
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_write_kernel(int64_t n, const int32_t* __restrict__ cnt,
+                                                                  const int64_t* __restrict__ toff,
+                                                                  int64_t* __restrict__ out) {
+  __shared__ int64_t wsum[kScanThreads / kWarp];
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanPer;
+  int64_t v[kScanPer];
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    const int64_t j = base + i;
+    v[i] = j < n ? cnt[j] : 0;
+    s += v[i];
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x / kWarp;
+  int64_t x = s;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[w] = x;
+  __syncthreads();
+  int64_t wo = 0;
+  for (int i = 0; i < w; ++i) wo += wsum[i];
+  int64_t run = toff[blockIdx.x] + wo + x - s;
+#pragma unroll
+  for (int i = 0; i < kScanPer; ++i) {
+    const int64_t j = base + i;
+    if (j < n) out[j] = run;
+    run += v[i];
+  }
+  if (base <= n - 1 && n - 1 < base + kScanPer) out[n] = run;
+}
+
+// Copies each entry into the band or the long-range matrix (keeping the row order), with
+// the values rounded to V.
+template <class V>
+__global__ void split_scatter_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                     const double* __restrict__ val, int band, const int64_t* __restrict__ rpb,
+                                     int32_t* __restrict__ cib, V* __restrict__ vb, const int64_t* __restrict__ rpl,
+                                     int32_t* __restrict__ cil, V* __restrict__ vl) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n;
+       row += (int64_t)gridDim.x * blockDim.x) {
+    int64_t b = rpb[row], l = rpl[row];
+    for (int64_t e = rp[row]; e < rp[row + 1]; ++e) {
+      const int c = ci[e];
+      const int64_t d = c > row ? c - row : row - c;
+      if (d <= band) cib[b] = c, vb[b] = (V)val[e], ++b;
+      else cil[l] = c, vl[l] = (V)val[e], ++l;
+    }
+  }
+}
+
 // Fraction of non-zeros with |col - row| <= b for b in kBands (one pass over the rows).
 __global__ void band_profile_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                     unsigned long long* counts, int nb, const int* bands) {
@@ -473,7 +877,7 @@ __global__ void __launch_bounds__(256) spmm_dense_kernel(int64_t n, const T* __r
 
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p,
-                     const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band) {
+                     const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band, bool pure) {
   if (n <= 0 || p <= 0) return;
   if (p > 32) throw std::invalid_argument("spmm: p > 32");
   constexpr int VEC = 16 / sizeof(T);
@@ -483,11 +887,22 @@ void launch_spmm_csr(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
     // two 16-byte vectors per lane halve the index work per gathered value
     const int lanes = (p + 2 * VEC - 1) / (2 * VEC);
     bool done = false;
-    if (lanes <= 1) done = csr_band_launch<T, V, 1, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 2) done = csr_band_launch<T, V, 2, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 4) done = csr_band_launch<T, V, 4, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else if (lanes <= 8) done = csr_band_launch<T, V, 8, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
-    else done = csr_band_launch<T, V, 16, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    if constexpr (std::is_same<T, float>::value && sizeof(V) == 4) {
+      if (pure) {
+        // L lanes per non-zero, one 16-byte vector each: L = pow2 >= nvec
+        const int nvec = (p + VEC - 1) / VEC;
+        if (nvec <= 2) done = csr_window_launch<T, V, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+        else if (nvec <= 4) done = csr_window_launch<T, V, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+        else done = csr_window_launch<T, V, 8>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+      }
+    }
+    if (!done) {
+      if (lanes <= 1) done = csr_band_launch<T, V, 1, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+      else if (lanes <= 2) done = csr_band_launch<T, V, 2, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+      else if (lanes <= 4) done = csr_band_launch<T, V, 4, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+      else if (lanes <= 8) done = csr_band_launch<T, V, 8, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+      else done = csr_band_launch<T, V, 16, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, band, st);
+    }
     if (done) return;
   }
   if (vec_ok) {
@@ -522,9 +937,66 @@ void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, in
 }
 
 template void launch_spmm_csr<double, double>(int64_t, const int64_t*, const int32_t*, const double*,
-                                              int, const double*, int, double*, int, cudaStream_t, int);
+                                              int, const double*, int, double*, int, cudaStream_t, int, bool);
 template void launch_spmm_csr<float, float>(int64_t, const int64_t*, const int32_t*, const float*,
-                                            int, const float*, int, float*, int, cudaStream_t, int);
+                                            int, const float*, int, float*, int, cudaStream_t, int, bool);
+
+template <class T, class V>
+void launch_spmm_csr_add(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
+                         T* Y, int ldy, cudaStream_t st) {
+  if (n <= 0 || p <= 0) return;
+  if (p > 32) throw std::invalid_argument("spmm: p > 32");
+  constexpr int VEC = 16 / sizeof(T);
+  const bool vec_ok = (ldx % VEC == 0) && (ldy % VEC == 0) && ldx >= round_up(p, VEC) &&
+                      !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15);
+  if (!vec_ok) throw std::invalid_argument("spmm add: blocks must be 16-byte aligned");
+  // L lanes x NV vectors cover the row: nvec 16-byte vectors per row of X
+  const int nvec = (p + VEC - 1) / VEC;
+  if (nvec <= 2) csr_add_launch<T, V, 1, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 3) csr_add_launch<T, V, 1, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 4) csr_add_launch<T, V, 1, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 6) csr_add_launch<T, V, 2, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 8) csr_add_launch<T, V, 2, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 12) csr_add_launch<T, V, 4, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else csr_add_launch<T, V, 4, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+}
+template void launch_spmm_csr_add<float, float>(int64_t, const int64_t*, const int32_t*, const float*, int,
+                                                const float*, int, float*, int, cudaStream_t);
+
+void split_csr_count(int64_t n, const int64_t* rp, const int32_t* ci, int band, int32_t* cb, int32_t* cl,
+                     cudaStream_t st) {
+  if (n <= 0) return;
+  split_count_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4864), 256, 0, st>>>(n, rp, ci, band, cb, cl);
+  LB_LAUNCH_CHECK();
+}
+
+int64_t split_scan_scratch(int64_t n) { return ceil_div(std::max<int64_t>(n, 1), kScanTile); }
+
+void split_csr_rowptr(int64_t n, const int32_t* cnt, int64_t* out, int64_t* scratch, cudaStream_t st) {
+  if (n <= 0) {
+    LB_CUDA(cudaMemsetAsync(out, 0, sizeof(int64_t), st));
+    return;
+  }
+  const int64_t ntiles = ceil_div(n, kScanTile);
+  scan_tile_sums_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(n, cnt, scratch);
+  LB_LAUNCH_CHECK();
+  scan_tile_offsets_kernel<<<1, 1024, 0, st>>>(ntiles, scratch);
+  LB_LAUNCH_CHECK();
+  scan_write_kernel<<<(unsigned)ntiles, kScanThreads, 0, st>>>(n, cnt, scratch, out);
+  LB_LAUNCH_CHECK();
+}
+
+template <class V>
+void split_csr_scatter(int64_t n, const int64_t* rp, const int32_t* ci, const double* val, int band,
+                       const int64_t* rpb, int32_t* cib, V* vb, const int64_t* rpl, int32_t* cil, V* vl,
+                       cudaStream_t st) {
+  if (n <= 0) return;
+  split_scatter_kernel<V><<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4864), 256, 0, st>>>(
+      n, rp, ci, val, band, rpb, cib, vb, rpl, cil, vl);
+  LB_LAUNCH_CHECK();
+}
+template void split_csr_scatter<float>(int64_t, const int64_t*, const int32_t*, const double*, int, const int64_t*,
+                                       int32_t*, float*, const int64_t*, int32_t*, float*, cudaStream_t);
 
 int profile_band(int64_t n, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st) {
   if (n <= 0 || nnz <= 0) return -1;

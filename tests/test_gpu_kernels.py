@@ -119,3 +119,36 @@ def test_ortho_against_matches_properties_and_oracle():
     assert np.max(np.abs(Q.T @ Q - np.eye(6))) <= 1e-14
     assert max_subspace_angle(Q, Qr) <= 1e-6
     assert st["passes"] >= 2
+
+
+def _f32_block(torch, X, ld):
+    """float32 row-major copy of X with leading dimension ld (a multiple of 4)."""
+    n, p = X.shape
+    buf = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+    buf[:, :p] = torch.from_numpy(X.astype(np.float32)).cuda()
+    return buf[:, :p]
+
+
+@pytest.mark.parametrize("n,p,band", [(50_001, 21, -1), (50_001, 16, 16), (20_011, 7, 0), (4_099, 32, 64),
+                                      (3_001, 5, -2), (1, 1, -1), (2_000, 3, 2048), (30_011, 12, 256)])
+def test_spmm_csr_f32_split_matches_oracle(n, p, band):
+    """FP32 band / long-range split product against the FP64 oracle on the FP32-rounded
+    operands: |Y - A32 X32| <= (nnz_row + 2) eps32 (|A32| |X32|) entrywise."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=n, seed=n) if n >= 600 else synth.tridiag_toeplitz(max(n, 1), 2.0, -1.0)
+    X = synth.gaussian_block(a.n, p, seed=7)
+    t = lb.upload_csr(a)
+    ld = (p + 3) // 4 * 4
+    Y, used = lb.spmm_csr_f32(t["row_ptr"], t["col_idx"], t["val"], _f32_block(torch, X, ld), band=band)
+    Y = Y.cpu().numpy().astype(np.float64)
+    a32 = synth.CSR(a.n, a.row_ptr, a.col_idx, a.val.astype(np.float32).astype(np.float64), a.diag)
+    X32 = X.astype(np.float32).astype(np.float64)
+    ref = oracle.apply(a32, X32)
+    scale = np.abs(a32.to_scipy()) @ np.abs(X32)
+    nz = int(np.max(np.diff(a.row_ptr))) + 2
+    assert np.all(np.abs(Y - ref) <= nz * np.finfo(np.float32).eps * scale + 1e-30)
+    if band >= 0:
+        assert used == band
+    elif band == -2:
+        assert used == -1
