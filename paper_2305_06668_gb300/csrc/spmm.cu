@@ -251,6 +251,18 @@ __device__ __forceinline__ void cp_async8_sp(void* smem, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
 }
 
+// Shared-memory loads by 32-bit shared-window address.
+__device__ __forceinline__ int2 lds_s32x2(unsigned addr) {
+  int2 r;
+  asm volatile("ld.shared.v2.s32 {%0, %1}, [%2];\n" : "=r"(r.x), "=r"(r.y) : "r"(addr));
+  return r;
+}
+__device__ __forceinline__ float4 lds_f32x4(unsigned addr) {
+  float4 r;
+  asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];\n" : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "r"(addr));
+  return r;
+}
+
 // Sum of a lane's V values over the G = 32/L lane groups of a warp, left scattered over
 // the lanes (a transpose reduction): at each xor level a lane keeps half of its values
 // (the upper half when its level bit is set) and adds the partner's copy of that half, so
@@ -460,6 +472,8 @@ bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   return true;
 }
 
+constexpr int kWindowPad = 64;  // staged entries beyond a sub-block that a batch may read
+
 // Band part of a split matrix (every entry has |col - row| <= band), FP32.  The CTA owns
 // rows [r0, r0 + R) and keeps rows [r0 - band, r0 + R + band) of X in shared memory (row
 // stride pp = p rounded up to 16 bytes), plus one zero row that the lanes past the end
@@ -470,13 +484,13 @@ bool csr_band_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
 // phase of a gather reads one contiguous row (free of bank conflicts); G = 32/L non-zeros
 // per warp step, UNR steps in flight, and a transpose reduction over the G groups.
 template <class T, class V, int L, int UNR, int RS>
-__global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(512, 1) spmm_csr_window_kernel(int64_t n, const int64_t* __restrict__ rp,
                                                               const int32_t* __restrict__ ci,
                                                               const V* __restrict__ val, int p,
                                                               const T* __restrict__ X, int ldx,
                                                               T* __restrict__ Y, int ldy, int R, int band,
                                                               int pp, int cap) {
-  static_assert(sizeof(V) == 4, "interleaved staging holds 4-byte values");
+  static_assert(sizeof(V) == 4 && sizeof(T) == 4, "FP32 blocks, interleaved 4-byte values");
   using VT = typename Vec16<T>::type;
   constexpr int VEC = Vec16<T>::n;
   constexpr int G = kWarp / L;
@@ -488,7 +502,9 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
   const int nvec = pp / VEC;
   T* tile = reinterpret_cast<T*>(smem_raw);                                                 // [win + 1][pp]
   int64_t* srp = reinterpret_cast<int64_t*>(smem_raw + (size_t)(win + 1) * pp * sizeof(T));  // [2][RS + 1]
-  int2* scv = reinterpret_cast<int2*>(srp + 2 * (RS + 1));                                // [2][cap] (col, val bits)
+  static_assert(G * UNR <= kWindowPad, "a batch may read kWindowPad entries past a sub-block's end");
+  const int cpad = cap + kWindowPad;  // entries read past a sub-block's end stay in the buffer
+  int2* scv = reinterpret_cast<int2*>(srp + 2 * (RS + 1));                                // [2][cpad]
   const int lane = threadIdx.x & 31;
   const int wid = threadIdx.x / kWarp, wpc = blockDim.x / kWarp;
   for (int e = threadIdx.x; e < win * nvec; e += blockDim.x) {
@@ -496,6 +512,10 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
     cp_async16_sp(tile + (int64_t)rr * pp + w * VEC, X + (lo + rr) * ldx + w * VEC);
   }
   for (int e = threadIdx.x; e < pp; e += blockDim.x) tile[(int64_t)win * pp + e] = T(0);
+  for (int e = threadIdx.x; e < 2 * cpad; e += blockDim.x) scv[e] = make_int2(0, 0);
+  __syncthreads();  // zeroed entries before any cp.async lands on them
+  const unsigned row_bytes = (unsigned)(pp * sizeof(T));
+  const unsigned zoff = (unsigned)win * row_bytes;
   const int nsub = (int)((r_end - r0 + RS - 1) / RS);
   auto bounds = [&](int k, int64_t& eb, int64_t& ee) {
     const int64_t a = r0 + (int64_t)k * RS, b = min(r_end, a + RS);
@@ -507,7 +527,7 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
     const int rows = (int)(min(r_end, a + RS) - a);
     for (int i = threadIdx.x; i <= rows; i += blockDim.x) cp_async8_sp(srp + buf * (RS + 1) + i, rp + a + i);
     if (ee - eb <= cap) {
-      int2* d = scv + buf * cap;
+      int2* d = scv + buf * cpad;
       for (int i = threadIdx.x; i < (int)(ee - eb); i += blockDim.x) {
         cp_async4_sp(&d[i].x, ci + eb + i);
         cp_async4_sp(&d[i].y, val + eb + i);
@@ -521,7 +541,8 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
   if (nsub > 1) bounds(1, nb, ne);
   const int g = lane / L, li = lane % L;
   const bool has_vec = li < nvec;
-  const T* tile_l = tile + li * VEC;
+  const char* tile_b = reinterpret_cast<const char*>(tile + li * VEC);
+  const unsigned tile_s = (unsigned)__cvta_generic_to_shared(tile_b);
   const int ilo = (int)lo;
   for (int k = 0; k < nsub; ++k) {
     const int buf = k & 1;
@@ -530,9 +551,17 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
     int64_t fb = 0, fe = 0;
     if (k + 2 < nsub) bounds(k + 2, fb, fe);  // in flight during this sub-block
     asm volatile("cp.async.wait_group 1;\n" ::);
+    if (ee - eb <= cap) {
+      // this thread's copies of sub-block k have landed: column index -> byte offset of
+      // its row in the window (clamped, so a malformed index stays in bounds)
+      int2* d = scv + buf * cpad;
+      for (int i = threadIdx.x; i < (int)(ee - eb); i += blockDim.x)
+        d[i].x = (int)(min((unsigned)(d[i].x - ilo), (unsigned)win) * row_bytes);
+    }
     __syncthreads();
     const bool staged = ee - eb <= cap;
-    const int2* sp = scv + buf * cap;
+    const int2* sp = scv + buf * cpad;
+    const unsigned sp_s = (unsigned)__cvta_generic_to_shared(sp);
     const int64_t* brp = srp + buf * (RS + 1);
     const int64_t rb = r0 + (int64_t)k * RS;
     const int rows = (int)(min(r_end, rb + RS) - rb);
@@ -541,29 +570,44 @@ __global__ void __launch_bounds__(512) spmm_csr_window_kernel(int64_t n, const i
       T acc[VEC];
 #pragma unroll
       for (int t = 0; t < VEC; ++t) acc[t] = T(0);
-      for (int lj = le0; lj < le1; lj += G * UNR) {
-        VT xv[UNR];
-        T vv[UNR];
+      if (staged) {
+        // branch-free: entries hold window byte offsets; lanes past the row end read the
+        // zero row (their value is a finite stale or zero entry)
+        for (int lj = le0; lj < le1; lj += G * UNR) {
+          const unsigned ea = sp_s + (unsigned)(lj + g) * 8u;  // entry address of step 0
+          const int rem = le1 - lj - g;                          // steps with u * G < rem are in the row
+          float4 xv[UNR];
+          float vv[UNR];
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) {
-          const int le = lj + u * G + g;
-          int c = ilo - 1;  // no entry: the zero row
-          T v = T(0);
-          if (le < le1) {
-            if (staged) {
-              const int2 cv = sp[le];
-              c = cv.x, v = (T)__int_as_float(cv.y);
-            } else {
-              c = ci[eb + le], v = (T)val[eb + le];
-            }
+          for (int u = 0; u < UNR; ++u) {
+            const int2 cv = lds_s32x2(ea + u * G * 8);
+            const unsigned off = u * G < rem ? (unsigned)cv.x : zoff;
+            vv[u] = __int_as_float(cv.y);
+            xv[u] = lds_f32x4(tile_s + off);
           }
-          vv[u] = v;
-          // in the window by construction (the clamp keeps a malformed index in bounds)
-          const unsigned o = min((unsigned)(c - ilo), (unsigned)win);
-          xv[u] = *reinterpret_cast<const VT*>(tile_l + (int)o * pp);
-        }
 #pragma unroll
-        for (int u = 0; u < UNR; ++u) vfma(vv[u], xv[u], acc);
+          for (int u = 0; u < UNR; ++u) vfma(vv[u], xv[u], acc);
+        }
+      } else {
+        for (int lj = le0; lj < le1; lj += G * UNR) {
+          VT xv[UNR];
+          T vv[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            const int le = lj + u * G + g;
+            unsigned off = zoff;
+            T v = T(0);
+            if (le < le1) {
+              // in the window by construction (the clamp keeps a malformed index in bounds)
+              off = min((unsigned)(ci[eb + le] - ilo), (unsigned)win) * row_bytes;
+              v = (T)val[eb + le];
+            }
+            vv[u] = v;
+            xv[u] = *reinterpret_cast<const VT*>(tile_b + off);
+          }
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) vfma(vv[u], xv[u], acc);
+        }
       }
       bool owner;
       const int off = reduce_scatter<L, VEC>(acc, lane, owner);
@@ -585,12 +629,12 @@ bool csr_window_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V*
                        T* Y, int ldy, int band, cudaStream_t st) {
   constexpr int VEC = 16 / sizeof(T);
   constexpr int RS = 64;
-  constexpr int UNR = L;  // G * UNR = 32 non-zeros per batch
+  constexpr int UNR = 2 * L;  // G * UNR = 64 non-zeros per batch (a typical band row)
   const int pp = round_up(p, VEC);
   if (ldx < pp || pp > L * VEC) return false;
   const size_t row_bytes = (size_t)pp * sizeof(T);
   const int cap = 4096;  // non-zeros per staged sub-block of RS rows
-  const size_t fixed = (size_t)2 * cap * sizeof(int2) + (size_t)2 * (RS + 1) * sizeof(int64_t);
+  const size_t fixed = (size_t)2 * (cap + kWindowPad) * sizeof(int2) + (size_t)2 * (RS + 1) * sizeof(int64_t);
   const size_t budget = 216 * 1024;
   if (budget <= fixed + row_bytes) return false;
   // rows per CTA: as many as fit beside the two band halos and the zero row
