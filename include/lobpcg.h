@@ -215,6 +215,12 @@ LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int 
  * values ascending; U: device, column-major s x s eigenvectors. */
 LOBPCG_API lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U, lobpcg_stream stream);
 
+/* Same contract, two-stage method (the Rayleigh-Ritz solve of the FP32 phase of the mixed
+ * form): FP32 Jacobi, one FP64 Cholesky-QR of its rotation matrix Q, then FP64 Jacobi on
+ * Q^T a Q accumulated into Q.  Eigenvalues and residuals to FP64 absolute accuracy
+ * (~eps ||a||), U orthonormal to FP64 rounding; exact zero couplings of a are not kept. */
+LOBPCG_API lobpcg_status lobpcg_syev2_f64(int s, const double* a, double* lam, double* U, lobpcg_stream stream);
+
 /* Algorithm 2 in place on X (n x p row-major, ldx, p <= 32).  stats (host, optional):
  * [0] Cholesky-QR passes, [1] shifted attempts, [2] SVQB steps, [3] cap hit (0/1). */
 LOBPCG_API lobpcg_status lobpcg_ortho_f64(int64_t n, int p, double* X, int ldx, double tau, int cap,

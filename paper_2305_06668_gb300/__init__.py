@@ -70,7 +70,7 @@ def lib():
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
-                     "lobpcg_spmm_csr_f32"):
+                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -273,13 +273,16 @@ def gram_noalloc(X, Y, out=None, stream=None):
     return Cm.t()
 
 
-def syev(a, stream=None):
+def syev(a, two_stage=False, stream=None):
+    """Eigenvalues (ascending) and eigenvectors of symmetric a; two_stage selects the
+    FP32-then-FP64 Jacobi used by the FP32 phase of the mixed form."""
     torch = _torch()
     s = a.shape[0]
     ac = a.t().contiguous()  # column-major storage of a
     lam = torch.empty(s, dtype=torch.float64, device=a.device)
     U = torch.empty((s, s), dtype=torch.float64, device=a.device)
-    _check(lib().lobpcg_syev_f64(C.c_int(s), _ptr(ac), _ptr(lam), _ptr(U), _stream(stream)))
+    fn = lib().lobpcg_syev2_f64 if two_stage else lib().lobpcg_syev_f64
+    _check(fn(C.c_int(s), _ptr(ac), _ptr(lam), _ptr(U), _stream(stream)))
     return lam, U.t()
 
 

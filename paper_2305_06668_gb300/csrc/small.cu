@@ -38,16 +38,20 @@ __device__ double block_max(double v, double* red) {
 
 // Parallel-order (round-robin) cyclic Jacobi on the symmetric s x s matrix a (column-
 // major, leading dimension lda, overwritten by its rotated form) accumulating the
-// rotations in V (s x s, ldv).  Each round applies s/2 disjoint rotations (classical
-// smaller-angle rotation of Golub & Van Loan, Sec. 8.5) as J^T A then A J.
-// Returns the number of sweeps, or -1 without convergence in 40 sweeps.
-__device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double* rot, double* red) {
+// rotations in V (s x s, ldv; set to the identity first when init_v).  Each round applies
+// s/2 disjoint rotations (classical smaller-angle rotation of Golub & Van Loan, Sec. 8.5)
+// as J^T A then A J, in the arithmetic of T.  Stops when off(a) <= rel_tol * ||a||_F.
+// Returns the number of sweeps, or -1 without convergence in max_sweeps.
+template <class T>
+__device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double* red, double rel_tol,
+                             int max_sweeps, bool init_v) {
   const int N = s + (s & 1);
   const int half = N / 2;
-  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
-    const int i = e % s, j = e / s;
-    V[i + j * ldv] = i == j ? 1.0 : 0.0;
-  }
+  if (init_v)
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      V[i + j * ldv] = i == j ? T(1) : T(0);
+    }
   double f2 = 0.0;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const double v = a[(e % s) + (e / s) * lda];
@@ -55,7 +59,7 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
   }
   const double fro = sqrt(block_sum(f2, red));
   int sweep = 0;
-  for (; sweep < 40; ++sweep) {
+  for (; sweep < max_sweeps; ++sweep) {
     double o2 = 0.0;
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
       const int i = e % s, j = e / s;
@@ -65,7 +69,7 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
       }
     }
     const double off = sqrt(block_sum(o2, red));
-    if (off <= 1e-15 * fro || off == 0.0) return sweep;
+    if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
       // phase A: rotation of every pair of this round (circle method, player N-1 fixed)
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
@@ -73,21 +77,21 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
         if (i == 0) p = N - 1, q = r;
         else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
         if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, sn = 0.0;
+        T c = T(1), sn = T(0);
         bool skip = q >= s;
         if (!skip) {
-          const double apq = a[p + q * lda];
-          if (apq == 0.0) {
+          const T apq = a[p + q * lda];
+          if (apq == T(0)) {
             skip = true;
           } else {
-            const double tau = (a[q + q * lda] - a[p + p * lda]) / (2.0 * apq);
-            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-            c = 1.0 / sqrt(1.0 + t * t);
+            const T tau = (a[q + q * lda] - a[p + p * lda]) / (T(2) * apq);
+            const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+            c = T(1) / sqrt(T(1) + t * t);
             sn = t * c;
           }
         }
-        rot[4 * i + 0] = skip ? -1.0 : (double)p;
-        rot[4 * i + 1] = (double)q;
+        rot[4 * i + 0] = skip ? T(-1) : (T)p;
+        rot[4 * i + 1] = (T)q;
         rot[4 * i + 2] = c;
         rot[4 * i + 3] = sn;
       }
@@ -95,13 +99,13 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
       // phase B: rows p, q of a (J^T A) and columns p, q of V (V J)
       for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
         const int i = e / s, j = e % s;
-        if (rot[4 * i] < 0.0) continue;
+        if (rot[4 * i] < T(0)) continue;
         const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
-        const double c = rot[4 * i + 2], sn = rot[4 * i + 3];
-        const double apj = a[p + j * lda], aqj = a[q + j * lda];
+        const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
+        const T apj = a[p + j * lda], aqj = a[q + j * lda];
         a[p + j * lda] = c * apj - sn * aqj;
         a[q + j * lda] = sn * apj + c * aqj;
-        const double vjp = V[j + p * ldv], vjq = V[j + q * ldv];
+        const T vjp = V[j + p * ldv], vjq = V[j + q * ldv];
         V[j + p * ldv] = c * vjp - sn * vjq;
         V[j + q * ldv] = sn * vjp + c * vjq;
       }
@@ -109,13 +113,13 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
       // phase C: columns p, q of a (A J); the annihilated pair is set to exactly zero
       for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
         const int i = e / s, j = e % s;
-        if (rot[4 * i] < 0.0) continue;
+        if (rot[4 * i] < T(0)) continue;
         const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
-        const double c = rot[4 * i + 2], sn = rot[4 * i + 3];
-        const double ajp = a[j + p * lda], ajq = a[j + q * lda];
-        double np = c * ajp - sn * ajq, nq = sn * ajp + c * ajq;
-        if (j == p) nq = 0.0;
-        if (j == q) np = 0.0;
+        const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
+        const T ajp = a[j + p * lda], ajq = a[j + q * lda];
+        T np = c * ajp - sn * ajq, nq = sn * ajp + c * ajq;
+        if (j == p) nq = T(0);
+        if (j == q) np = T(0);
         a[j + p * lda] = np;
         a[j + q * lda] = nq;
       }
@@ -125,42 +129,119 @@ __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double*
   return -1;
 }
 
-// Write eigenvalues (diagonal of the rotated a) ascending with their V columns;
-// ties keep index order.
-__device__ void sort_eig(int s, const double* a, int lda, const double* V, int ldv, double* lam,
-                         double* U) {
-  for (int i = threadIdx.x; i < s; i += blockDim.x) {
-    const double li = a[i + i * lda];
-    int rank = 0;
-    for (int j = 0; j < s; ++j) {
-      const double lj = a[j + j * lda];
-      rank += (lj < li) || (lj == li && j < i);
-    }
-    lam[rank] = li;
-    for (int r = 0; r < s; ++r) U[r + rank * s] = V[r + i * ldv];
-  }
+__device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double* rot, double* red) {
+  return jacobi_sweeps<double>(s, a, lda, V, ldv, rot, red, 1e-15, 40, true);
 }
 
+__device__ int chol_cta(int p, double* L, int ld, int* flag);
+
+// Rayleigh-Ritz eigensolve of the symmetric s x s matrix a; eigenvalues ascending (ties
+// keep index order) with their eigenvector columns.
+//
+// TWO_STAGE = false: FP64 parallel-order Jacobi from a (the oracle's method).
+//
+// TWO_STAGE = true, in two precisions: FP32 Jacobi first diagonalises a (FP32 runs at
+// about 60x the FP64 rate on this part); its rotation matrix, made orthonormal in FP64 by
+// one Cholesky-QR step, gives Q with Q^T a Q diagonal up to ~1e-7 relative.  FP64 Jacobi
+// then finishes on Q^T a Q, accumulating its rotations into Q, in about 2 sweeps instead of
+// the ~7 it takes from a.  Off-diagonal mass ends <= 1e-15 ||a||_F with Q orthonormal to
+// FP64 rounding, but forming Q^T a Q puts absolute errors of order eps ||a|| in every entry,
+// so exact zero couplings (and the relative accuracy plain Jacobi keeps for small
+// eigenvalues of a graded matrix) are not preserved.
+template <bool TWO_STAGE>
 __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double* __restrict__ a_in,
                                                              int upper_only, double* __restrict__ lam,
                                                              double* __restrict__ U, int* sweeps_out) {
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double rot[4 * (kMaxS / 2 + 1)];
-  const int lda = s + 1;  // odd stride against bank conflicts
-  double* a = sm;
-  double* V = sm + s * lda;
+  __shared__ int rank[kMaxS];
+  __shared__ int flag;
+  const int ld = s + 1;  // odd stride against bank conflicts
+  double* A = sm;
+  double* B = A + s * ld;
+  double* C = B + s * ld;
   for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
     const int i = e % s, j = e / s;
     double v;
     if (upper_only) v = i <= j ? a_in[i + j * s] : a_in[j + i * s];
     else v = 0.5 * (a_in[i + j * s] + a_in[j + i * s]);
-    a[i + j * lda] = v;
+    A[i + j * ld] = v;
+  }
+  int sw;
+  if (!TWO_STAGE) {
+    __syncthreads();
+    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, 1e-15, 40, true);
+  } else {
+    // ---- FP32 pass (a32 and its rotations share the C buffer)
+    float* a32 = reinterpret_cast<float*>(C);
+    float* v32 = a32 + s * ld;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) a32[(e % s) + (e / s) * ld] = (float)A[(e % s) + (e / s) * ld];
+    __syncthreads();
+    jacobi_sweeps<float>(s, a32, ld, v32, ld, reinterpret_cast<float*>(rot), red, 2e-6, 20, true);
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) B[(e % s) + (e / s) * ld] = (double)v32[(e % s) + (e / s) * ld];
+    __syncthreads();
+    // ---- Q = B L^{-T} with L L^T = B^T B (Cholesky-QR in FP64)
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      if (i >= j) {
+        double acc = 0.0;
+        for (int r = 0; r < s; ++r) acc += B[r + i * ld] * B[r + j * ld];
+        C[i + j * ld] = acc;
+      }
+    }
+    __syncthreads();
+    const int bad = chol_cta(s, C, ld, &flag);
+    if (bad) {
+      // cannot happen for a rotation product; start the FP64 pass from the identity instead
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) B[(e % s) + (e / s) * ld] = (e % s) == (e / s) ? 1.0 : 0.0;
+    } else {
+      for (int r = threadIdx.x; r < s; r += blockDim.x)  // row r of B solves x L^T = b
+        for (int j = 0; j < s; ++j) {
+          double acc = B[r + j * ld];
+          for (int i = 0; i < j; ++i) acc -= B[r + i * ld] * C[j + i * ld];
+          B[r + j * ld] = acc / C[j + j * ld];
+        }
+    }
+    __syncthreads();
+    // ---- A <- Q^T a Q (C = a Q, then the upper triangle of Q^T C, mirrored)
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      double acc = 0.0;
+      for (int t = 0; t < s; ++t) acc += A[i + t * ld] * B[t + j * ld];
+      C[i + j * ld] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      if (i <= j) {
+        double acc = 0.0;
+        for (int t = 0; t < s; ++t) acc += B[t + i * ld] * C[t + j * ld];
+        A[i + j * ld] = acc;
+        A[j + i * ld] = acc;
+      }
+    }
+    __syncthreads();
+    // ---- FP64 pass, rotations accumulated into Q
+    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, 1e-15, 40, false);
   }
   __syncthreads();
-  const int sw = jacobi_cta(s, a, lda, V, lda, rot, red);
+  for (int i = threadIdx.x; i < s; i += blockDim.x) {
+    const double li = A[i + i * ld];
+    int r = 0;
+    for (int j = 0; j < s; ++j) {
+      const double lj = A[j + j * ld];
+      r += (lj < li) || (lj == li && j < i);
+    }
+    rank[i] = r;
+    lam[r] = li;
+  }
   __syncthreads();
-  sort_eig(s, a, lda, V, lda, lam, U);
+  for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+    const int r = e % s, i = e / s;
+    U[r + rank[i] * s] = B[r + i * ld];
+  }
   if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
 }
 
@@ -529,17 +610,21 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
 }  // namespace
 
 void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U, int* sweeps_out,
-                 cudaStream_t st) {
+                 cudaStream_t st, bool two_stage) {
   if (s <= 0) return;
   if (s > kMaxS) throw std::invalid_argument("syev: s > 96");
-  const size_t smem = (size_t)2 * s * (s + 1) * sizeof(double);
+  const size_t smem = (size_t)(two_stage ? 3 : 2) * s * (s + 1) * sizeof(double);
   // set once per process; function-local statics initialise thread-safely
   static const bool attr = [&] {
-    LB_CUDA(cudaFuncSetAttribute(syev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * kMaxS * (kMaxS + 1) * 8));
+    LB_CUDA(cudaFuncSetAttribute(syev_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 2 * kMaxS * (kMaxS + 1) * 8));
+    LB_CUDA(cudaFuncSetAttribute(syev_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 3 * kMaxS * (kMaxS + 1) * 8));
     return true;
   }();
   (void)attr;
-  syev_kernel<<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
+  if (two_stage) syev_kernel<true><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
+  else syev_kernel<false><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
   LB_LAUNCH_CHECK();
 }
 

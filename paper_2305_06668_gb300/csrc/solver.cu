@@ -361,10 +361,11 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
   const int q = Y.width();
   int passes = 0;
   double last = 0.0;
+  bool c_ready = false;  // C = Y^T W of the current W is already in c.C (the previous pass's test)
   c.prof.mark(PH_ORTHO);
   for (;;) {
     if (q > 0) {
-      gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);    // C = Y^T W
+      if (!c_ready) gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);  // C = Y^T W
       UpdateJob<T> job{};
       job.in[0] = Y;
       job.out[0] = W;
@@ -387,6 +388,7 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
       c.stats.cap_hits++;
       break;
     }
+    c_ready = true;
   }
   if (q > 0 && kept && !(last <= std::sqrt(tau))) {
     // R16: keep the columns whose overlap with Y is at most sqrt(tau)
@@ -472,7 +474,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   ortho<T>(c, b.X[0], ld, m, tau, cap);                                 // X0 <- ortho(X0)
   apply_A<T>(c, b.X[0], ld, m, b.AX[0], ld);                            // AX = A X
   gram<T>(c, cols1<T>(b.X[0], ld, m), cols1<T>(b.AX[0], ld, m), true, c.G);  // a = X^T AX
-  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st);          // a u = u lambda
+  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4);  // a u = u lambda
   LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
   {
     UpdateJob<T> job{};
@@ -535,7 +537,9 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     c.prof.mark(PH_RR_GRAM);
     gram<T>(c, V, AV, true, c.G);                                       // a = V^T AV (upper)
     c.prof.mark(PH_RR_EIG);
-    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st);        // Rayleigh-Ritz
+    // Rayleigh-Ritz; the FP32 phase, whose Ritz vectors go to FP32 blocks, takes the
+    // two-stage solver, the FP64 phase the plain FP64 Jacobi
+    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4);
     c.prof.mark(PH_UPDATE);
     LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
     const int nxt = cur ^ 1;
@@ -1012,6 +1016,17 @@ extern "C" lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, do
     require(s >= 1 && s <= kMaxS && a && lam && U, "lobpcg_syev_f64: need 1 <= s <= 96 and non-NULL arrays");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     launch_syev(s, a, false, lam, U, nullptr, st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_syev2_f64(int s, const double* a, double* lam, double* U,
+                                          lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(s >= 1 && s <= kMaxS && a && lam && U, "lobpcg_syev2_f64: need 1 <= s <= 96 and non-NULL arrays");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    launch_syev(s, a, false, lam, U, nullptr, st, true);
     LB_CUDA(cudaStreamSynchronize(st));
     return LOBPCG_OK;
   });

@@ -62,14 +62,15 @@ def test_gram_matches_oracle(n, p, q):
     assert np.all(np.abs(Cg - ref) <= 8 * np.finfo(float).eps * np.log2(n + 2) * 16 * scale + 1e-300)
 
 
+@pytest.mark.parametrize("two_stage", [False, True])
 @pytest.mark.parametrize("s", [1, 2, 5, 12, 48, 95, 96])
-def test_syev_matches_oracle_jacobi(s):
+def test_syev_matches_oracle_jacobi(s, two_stage):
     torch = cuda()
     import paper_2305_06668_gb300 as lb
     g = np.random.default_rng(s)
     a = g.standard_normal((s, s))
     a = 0.5 * (a + a.T)
-    lam, U = lb.syev(torch.from_numpy(a).cuda())
+    lam, U = lb.syev(torch.from_numpy(a).cuda(), two_stage=two_stage)
     lam, U = lam.cpu().numpy(), U.cpu().numpy()
     lr, Ur, _ = oracle.jacobi_eig(a)
     nrm = max(1.0, np.linalg.norm(a))
@@ -152,3 +153,26 @@ def test_spmm_csr_f32_split_matches_oracle(n, p, band):
         assert used == band
     elif band == -2:
         assert used == -1
+
+
+@pytest.mark.parametrize("two_stage", [False, True])
+@pytest.mark.parametrize("s", [7, 63, 96])
+def test_syev_clustered_and_repeated_eigenvalues(s, two_stage):
+    """Repeated and 1e-12-close eigenvalues: eigenvalues to 1e-13 ||a||, U orthonormal to
+    1e-13 s and a U = U diag(lam) to 1e-13 ||a|| (vectors of a cluster are not unique)."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(1000 + s)
+    lam = np.sort(g.uniform(-1.0, 1.0, s))
+    lam[: s // 3] = lam[0]                       # a repeated eigenvalue
+    lam[s // 3: s // 3 + 3] = lam[s // 3] + np.array([0.0, 1e-12, 2e-12])  # a tight cluster
+    lam = np.sort(lam)
+    Q, _ = np.linalg.qr(g.standard_normal((s, s)))
+    a = (Q * lam) @ Q.T
+    a = 0.5 * (a + a.T)
+    lg, U = lb.syev(torch.from_numpy(a).cuda(), two_stage=two_stage)
+    lg, U = lg.cpu().numpy(), U.cpu().numpy()
+    nrm = max(1.0, np.linalg.norm(a))
+    assert np.max(np.abs(lg - lam)) <= 1e-13 * nrm
+    assert np.max(np.abs(U.T @ U - np.eye(s))) <= 1e-13 * s
+    assert np.max(np.abs(a @ U - U * lg)) <= 1e-13 * nrm
