@@ -658,12 +658,13 @@ bool csr_window_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V*
   return true;
 }
 
-// Long-range part of a split product: Y += A_lr X.  A_lr holds the few couplings per row
-// that lie outside the band, so the rows of X it reads are scattered over the whole
-// block.  Each group of L lanes owns one row of Y (NV 16-byte vectors per lane, no
-// cross-lane reduction) and walks that row's entries UNR at a time, issuing all UNR
-// gathers before using them; a warp thus keeps G = 32/L rows x UNR gathers in flight.
-template <class T, class V, int L, int NV, int UNR>
+// Row-parallel product, Y += A X (ACC) or Y = A X.  Each group of L lanes owns one row of
+// Y (NV 16-byte vectors per lane, no cross-lane reduction) and walks that row's entries
+// UNR at a time, issuing all UNR gathers before using them; a warp thus keeps G = 32/L
+// rows x UNR gathers in flight.  Used for the long-range part of a split product (few,
+// scattered entries per row) and for FP64 products, which are bound by the FP64 FMA rate:
+// here nearly every lane of every FMA instruction does useful work.
+template <class T, class V, int L, int NV, int UNR, bool ACC>
 __global__ void __launch_bounds__(256) spmm_csr_add_kernel(int64_t n, const int64_t* __restrict__ rp,
                                                            const int32_t* __restrict__ ci,
                                                            const V* __restrict__ val, int p,
@@ -680,7 +681,7 @@ __global__ void __launch_bounds__(256) spmm_csr_add_kernel(int64_t n, const int6
   for (int64_t row = ((int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * G + g; row < n;
        row += groups) {
     const int64_t e0 = rp[row], e1 = rp[row + 1];
-    if (e0 == e1 || !has_cols) continue;
+    if ((ACC && e0 == e1) || !has_cols) continue;
     T acc[NV][VEC];
 #pragma unroll
     for (int w = 0; w < NV; ++w)
@@ -708,7 +709,7 @@ __global__ void __launch_bounds__(256) spmm_csr_add_kernel(int64_t n, const int6
     for (int w = 0; w < NV; ++w) {
       const int cw = col0 + w * VEC;
       if (cw + VEC <= p) {
-        VT y = *reinterpret_cast<const VT*>(yr + w * VEC);
+        VT y = ACC ? *reinterpret_cast<const VT*>(yr + w * VEC) : VT{};
         T* py = reinterpret_cast<T*>(&y);
 #pragma unroll
         for (int t = 0; t < VEC; ++t) py[t] += acc[w][t];
@@ -716,13 +717,13 @@ __global__ void __launch_bounds__(256) spmm_csr_add_kernel(int64_t n, const int6
       } else {
 #pragma unroll
         for (int t = 0; t < VEC; ++t)
-          if (cw + t < p) yr[w * VEC + t] += acc[w][t];
+          if (cw + t < p) yr[w * VEC + t] = ACC ? yr[w * VEC + t] + acc[w][t] : acc[w][t];
       }
     }
   }
 }
 
-template <class T, class V, int L, int NV>
+template <class T, class V, int L, int NV, bool ACC>
 void csr_add_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
                     T* Y, int ldy, cudaStream_t st) {
   int dev = 0, sms = 152;
@@ -732,8 +733,23 @@ void csr_add_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V* va
   constexpr int G = kWarp / L;
   int64_t ctas = std::min<int64_t>(ceil_div(n, (threads / kWarp) * G), (int64_t)sms * 6);
   if (ctas < 1) ctas = 1;
-  spmm_csr_add_kernel<T, V, L, NV, 4><<<(unsigned)ctas, threads, 0, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy);
+  spmm_csr_add_kernel<T, V, L, NV, 4, ACC><<<(unsigned)ctas, threads, 0, st>>>(n, rp, ci, val, p, X, ldx, Y, ldy);
   LB_LAUNCH_CHECK();
+}
+
+// L lanes x NV vectors cover the row: nvec 16-byte vectors per row of X
+template <class T, class V, bool ACC>
+void csr_rows_dispatch(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,
+                       T* Y, int ldy, cudaStream_t st) {
+  constexpr int VEC = 16 / sizeof(T);
+  const int nvec = (p + VEC - 1) / VEC;
+  if (nvec <= 2) csr_add_launch<T, V, 1, 2, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 3) csr_add_launch<T, V, 1, 3, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 4) csr_add_launch<T, V, 1, 4, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 6) csr_add_launch<T, V, 2, 3, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 8) csr_add_launch<T, V, 2, 4, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else if (nvec <= 12) csr_add_launch<T, V, 4, 3, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  else csr_add_launch<T, V, 4, 4, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
 }
 
 // ---- band / long-range split of a CSR matrix (once, when the solver is created) ----
@@ -927,6 +943,13 @@ void launch_spmm_csr(int64_t n, const int64_t* rp, const int32_t* ci, const V* v
   constexpr int VEC = 16 / sizeof(T);
   const bool vec_ok = (ldx % VEC == 0) && (ldy % VEC == 0) && ldx >= round_up(p, VEC) &&
                       !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15);
+  if constexpr (std::is_same<T, double>::value) {
+    if (vec_ok) {
+      // FP64 is bound by the FMA rate: the row-parallel kernel keeps every lane busy
+      csr_rows_dispatch<T, V, false>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+      return;
+    }
+  }
   if (vec_ok && band >= 0) {
     // two 16-byte vectors per lane halve the index work per gathered value
     const int lanes = (p + 2 * VEC - 1) / (2 * VEC);
@@ -994,15 +1017,7 @@ void launch_spmm_csr_add(int64_t n, const int64_t* rp, const int32_t* ci, const 
   const bool vec_ok = (ldx % VEC == 0) && (ldy % VEC == 0) && ldx >= round_up(p, VEC) &&
                       !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15);
   if (!vec_ok) throw std::invalid_argument("spmm add: blocks must be 16-byte aligned");
-  // L lanes x NV vectors cover the row: nvec 16-byte vectors per row of X
-  const int nvec = (p + VEC - 1) / VEC;
-  if (nvec <= 2) csr_add_launch<T, V, 1, 2>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else if (nvec <= 3) csr_add_launch<T, V, 1, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else if (nvec <= 4) csr_add_launch<T, V, 1, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else if (nvec <= 6) csr_add_launch<T, V, 2, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else if (nvec <= 8) csr_add_launch<T, V, 2, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else if (nvec <= 12) csr_add_launch<T, V, 4, 3>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
-  else csr_add_launch<T, V, 4, 4>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+  csr_rows_dispatch<T, V, true>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
 }
 template void launch_spmm_csr_add<float, float>(int64_t, const int64_t*, const int32_t*, const float*, int,
                                                 const float*, int, float*, int, cudaStream_t);
