@@ -47,14 +47,14 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
-def make_problem():
+def make_problem(n_rows=N_ROWS):
     import synth
-    cache = f"/tmp/lobpcg_bench_ci_{N_ROWS}_{SEED}.npz"
+    cache = f"/tmp/lobpcg_bench_ci_{n_rows}_{SEED}.npz"
     if os.path.exists(cache):
         z = np.load(cache)
         a = synth.CSR(n=int(z["n"]), row_ptr=z["row_ptr"], col_idx=z["col_idx"], val=z["val"], diag=z["diag"])
     else:
-        a = synth.sparse_ci(n=N_ROWS, seed=SEED)
+        a = synth.sparse_ci(n=n_rows, seed=SEED)
         try:
             np.savez(cache, n=a.n, row_ptr=a.row_ptr, col_idx=a.col_idx, val=a.val, diag=a.diag)
         except OSError:
@@ -182,7 +182,7 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2305_06668_gb300 as lb
 
-    a, x0_np = make_problem()
+    a, x0_np = make_problem(args.n)
     t = lb.upload_csr(a)
     x0 = torch.from_numpy(x0_np).cuda()
     stream = torch.cuda.current_stream()
@@ -217,6 +217,13 @@ def run_ours(args):
     statuses = [s for s, *_ in infos]
     last = infos[-1][1]
 
+    if args.profile:
+        # profiling run (ncu): the timed solves only
+        mixed.close()
+        if rank == 0:
+            print(json.dumps({"profile_run": True, "n": a.n, "s_per_solve": per_solve,
+                              "iterations": last["iterations"], "status": [lb.STATUS_NAMES[s] for s in statuses]}))
+        return 0
     # plain FP64 GPU solve of the same problem (the comparison the metric names)
     fp64 = lb.Solver(**t, extra=EXTRA, precision=lb.FP64, profile=True, maxiter=args.maxiter)
     r64 = fp64.solve(K, TOL, X0=x0)
@@ -379,8 +386,13 @@ def main():
     ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched"],
                     help="ci2m: the headline workload; batched: the 256-problem serving workload")
     ap.add_argument("--nprob", type=int, default=256)
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
+    ap.add_argument("--n", type=int, default=N_ROWS, help="rows of the CI-like matrix (profiling runs only)")
     ap.add_argument("--threads", type=int, default=32)
     args = ap.parse_args()
+    if args.n != N_ROWS and not args.profile:
+        ap.error("--n changes the workload: only for --profile runs")
     if args.config == "batched":
         return run_batched(args)
     if args.impl == "reference":
