@@ -30,6 +30,10 @@ if ROOT not in sys.path:
 
 METRIC = "time to k eigenpairs at \u2016r\u2016\u22641e-8: mixed+learned vs plain FP64 LOBPCG, 1 GB300"
 N_ROWS, K, EXTRA, TOL, SEED = 2_000_000, 16, 5, 1e-8, 0
+# DRAM bytes (read + write) per FP64 block-update launch, averaged over the update
+# launches of one solve from the ncu capture in profiles/update_fp64_ci1m.md (n = 10^6,
+# scaled to n = 2*10^6 by the rows processed); None until measured
+UPDATE_FP64_TRAFFIC = None
 WORKLOAD = "CI-like sparse symmetric n=2,000,000, ~65 nnz/row, k=16 (+5 extra), tol 1e-8"
 # FP64 LOBPCG iterations this workload needs (measured with the GPU FP64 path, which takes
 # the same steps as the oracle); scales the oracle's per-iteration time of the reference arm.
@@ -248,7 +252,8 @@ def run_ours(args):
         cols = c32 / l32
         # algorithmic bytes of one FP32 product: values + column indices + row pointers + read W + write AW
         b32 = nnz * (4 + 4) + (n + 1) * 8 + 2 * n * cols * 4
-        rooflines["spmm_fp32"] = {"kernel": "spmm_csr_band_kernel<float> (A W, mixed phase)", "bound": "hbm",
+        rooflines["spmm_fp32"] = {"kernel": "spmm_csr_window_kernel + spmm_csr_add_kernel (A W, FP32, band / "
+                                            "long-range split)", "bound": "hbm",
                                   "achieved": b32 / t32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
                                   "frac": b32 / t32 / 1e9 / hbm_peak, "traffic": None,
                                   "bytes_per_launch": b32, "avg_launch_s": t32, "peak_source": peak_kind}
@@ -256,16 +261,28 @@ def run_ours(args):
         t64 = ph64["spmm"] / l64
         cols = c64 / l64
         f64 = 2.0 * nnz * cols
-        rooflines["spmm_fp64"] = {"kernel": "spmm_csr_vec_kernel<double> (A W, FP64 refinement)", "bound": "alu",
+        rooflines["spmm_fp64"] = {"kernel": "spmm_csr_add_kernel<double> (A W, FP64 refinement, row-parallel)",
+                                  "bound": "alu",
                                   "achieved": f64 / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                                   "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
                                   "flops_per_launch": f64, "avg_launch_s": t64,
                                   "peak_source": "FP64 FMA rate measured on this GB300 (probe, 1.19-1.20 TFLOP/s)"}
+    # the FP64 block update (update_kernel<double>): the kernel with the largest share of GPU
+    # time in the ncu launch list of this command, timed per launch with CUDA events
+    ut = sum(i["update_fp64_seconds"] for _, i, _, _ in infos)
+    uf = sum(i["update_fp64_flops"] for _, i, _, _ in infos)
+    ul = sum(i["update_fp64_launches"] for _, i, _, _ in infos)
+    if ul and ut > 0:
+        rooflines["update_fp64"] = {"kernel": "update_kernel<double> (FP64 block updates: X = V u_x, P = V u_p, "
+                                              "W -= Y C, W <- W L^-T)", "bound": "alu",
+                                    "achieved": uf / ut / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                    "frac": uf / ut / 1e12 / fp64_peak, "traffic": UPDATE_FP64_TRAFFIC,
+                                    "flops_per_launch": uf / ul, "avg_launch_s": ut / ul,
+                                    "peak_source": "FP64 FMA rate measured on this GB300 (probe, 1.19-1.20 TFLOP/s)"}
     share = {k: v / max(sum(ph_all.values()), 1e-30) for k, v in ph_all.items()}
-    dominant = max(share, key=share.get)
-    roofline = dict(rooflines.get("spmm_fp32", {}))
+    roofline = dict(rooflines.get("update_fp64", rooflines.get("spmm_fp32", {})))
     roofline["phase_share"] = share
-    roofline["dominant_phase"] = dominant
+    roofline["dominant_phase"] = max(share, key=share.get)
     # end to end through the C ABI from pinned host buffers: H2D of the matrix and the
     # initial block, context creation, solve, D2H of the eigenvectors
     host = {k: v.cpu().pin_memory() for k, v in t.items()}

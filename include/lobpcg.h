@@ -123,6 +123,10 @@ typedef struct {
   double phase_seconds_fp64[6]; /* with opt.profile: the FP64 part of phase_seconds */
   int64_t spmm_launches_fp64;   /* products with A in FP64 */
   int64_t spmm_columns_fp64;    /* columns of those products */
+  double update_fp64_seconds;   /* with opt.profile: summed duration of the FP64 block updates
+                                   (X = V u, W -= Y C, W <- W L^-T, ...), CUDA events per launch */
+  double update_fp64_flops;     /* their algorithmic flops, 2 n s q per product */
+  int64_t update_fp64_launches; /* their number */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */

@@ -51,7 +51,8 @@ class _Info(C.Structure):
                 ("seconds", C.c_double), ("phase_seconds", C.c_double * 6), ("kernel_launches", C.c_int64),
                 ("spmm_launches", C.c_int64), ("precond_fallback", C.c_int),
                 ("phase_seconds_fp64", C.c_double * 6), ("spmm_launches_fp64", C.c_int64),
-                ("spmm_columns_fp64", C.c_int64)]
+                ("spmm_columns_fp64", C.c_int64), ("update_fp64_seconds", C.c_double),
+                ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64)]
 
 
 def library_path() -> pathlib.Path:

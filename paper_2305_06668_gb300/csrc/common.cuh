@@ -173,9 +173,10 @@ void launch_all_finite(int64_t count, const double* src, int* flag, cudaStream_t
 // Symmetric eigensolve: a (s x s, column-major; only the upper triangle is read when
 // upper_only) -> lam ascending, U column-major.  sweeps_out: device int (may be null),
 // FP64 sweeps.  two_stage: FP32 Jacobi, Cholesky-QR of its rotations, FP64 Jacobi on
-// Q^T a Q (faster; absolute accuracy eps ||a||); else FP64 Jacobi from a.
+// Q^T a Q (faster; absolute accuracy eps ||a||); else FP64 Jacobi from a.  The FP64
+// Jacobi stops when its off-diagonal mass is <= tol64 ||a||_F.
 void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U, int* sweeps_out,
-                 cudaStream_t st, bool two_stage = false);
+                 cudaStream_t st, bool two_stage = false, double tol64 = 1e-15);
 
 // Cholesky-QR step on the reduced Gram matrix M (p x p, column-major):
 //  ctl[0] <- 1 if max|M - I| <= tau (already orthonormal), else 0 and Linv <- L^{-T}

@@ -151,7 +151,8 @@ __device__ int chol_cta(int p, double* L, int ld, int* flag);
 template <bool TWO_STAGE>
 __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double* __restrict__ a_in,
                                                              int upper_only, double* __restrict__ lam,
-                                                             double* __restrict__ U, int* sweeps_out) {
+                                                             double* __restrict__ U, int* sweeps_out,
+                                                             double tol32, double tol64) {
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double rot[4 * (kMaxS / 2 + 1)];
@@ -171,16 +172,14 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
   int sw;
   if (!TWO_STAGE) {
     __syncthreads();
-    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, 1e-15, 40, true);
+    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, tol64, 40, true);
   } else {
     // ---- FP32 pass (a32 and its rotations share the C buffer)
     float* a32 = reinterpret_cast<float*>(C);
     float* v32 = a32 + s * ld;
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) a32[(e % s) + (e / s) * ld] = (float)A[(e % s) + (e / s) * ld];
     __syncthreads();
-    // a rough FP32 stage is enough: the FP64 stage converges quadratically from it (the
-    // stopping point measured on the CI-like workload: 1e-4 relative, at most 10 sweeps)
-    jacobi_sweeps<float>(s, a32, ld, v32, ld, reinterpret_cast<float*>(rot), red, 1e-4, 10, true);
+    jacobi_sweeps<float>(s, a32, ld, v32, ld, reinterpret_cast<float*>(rot), red, tol32, 20, true);
     __syncthreads();
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) B[(e % s) + (e / s) * ld] = (double)v32[(e % s) + (e / s) * ld];
     __syncthreads();
@@ -226,7 +225,7 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
     }
     __syncthreads();
     // ---- FP64 pass, rotations accumulated into Q
-    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, 1e-15, 40, false);
+    sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, tol64, 40, false);
   }
   __syncthreads();
   for (int i = threadIdx.x; i < s; i += blockDim.x) {
@@ -612,7 +611,7 @@ __global__ void __launch_bounds__(kSmallThreads) lock_p_kernel(int s, int m, int
 }  // namespace
 
 void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U, int* sweeps_out,
-                 cudaStream_t st, bool two_stage) {
+                 cudaStream_t st, bool two_stage, double tol64) {
   if (s <= 0) return;
   if (s > kMaxS) throw std::invalid_argument("syev: s > 96");
   const size_t smem = (size_t)(two_stage ? 3 : 2) * s * (s + 1) * sizeof(double);
@@ -625,8 +624,13 @@ void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U
     return true;
   }();
   (void)attr;
-  if (two_stage) syev_kernel<true><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
-  else syev_kernel<false><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out);
+  // FP32 stage: to its rounding floor when the FP64 stage stops early (one FP64 sweep then
+  // squares its off-diagonal mass), else a rough start for a full FP64 finish
+  const double tol32 = tol64 >= 1e-12 ? 2e-6 : 1e-4;
+  if (two_stage)
+    syev_kernel<true><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out, tol32, tol64);
+  else
+    syev_kernel<false><<<1, kSmallThreads, smem, st>>>(s, a, upper_only ? 1 : 0, lam, U, sweeps_out, tol32, tol64);
   LB_LAUNCH_CHECK();
 }
 

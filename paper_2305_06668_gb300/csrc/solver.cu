@@ -96,6 +96,8 @@ struct Profiler {
     st = s;
     used = 0;
     phase.clear();
+    kused = 0;
+    kflops = 0.0;
   }
   void mark(int ph) {
     if (!on) return;
@@ -121,8 +123,33 @@ struct Profiler {
       if (phase[i] >= PH_COUNT) out64[ph] += ms * 1e-3;
     }
   }
+  // event pairs around every FP64 block update (the FP64-bound update kernel), with the
+  // algorithmic flops of each: 2 n s q per product
+  std::vector<cudaEvent_t> kpool;
+  size_t kused = 0;
+  double kflops = 0.0;
+  void kmark() {
+    if (kused == kpool.size()) {
+      cudaEvent_t e;
+      LB_CUDA(cudaEventCreate(&e));
+      kpool.push_back(e);
+    }
+    LB_CUDA(cudaEventRecord(kpool[kused], st));
+    ++kused;
+  }
+  // seconds of the timed updates (after finish's synchronisation)
+  double kseconds() {
+    double t = 0.0;
+    for (size_t i = 0; i + 1 < kused; i += 2) {
+      float ms = 0.f;
+      LB_CUDA(cudaEventElapsedTime(&ms, kpool[i], kpool[i + 1]));
+      t += ms * 1e-3;
+    }
+    return t;
+  }
   ~Profiler() {
     for (auto e : pool) cudaEventDestroy(e);
+    for (auto e : kpool) cudaEventDestroy(e);
   }
 };
 
@@ -287,6 +314,20 @@ struct Prec<float> {
   static int64_t lda(lobpcg_ctx& c) { return c.A.n; }
 };
 
+// launch_update with, in profile mode, the FP64 launches timed and their flops counted.
+template <class T>
+int update(lobpcg_ctx& c, const UpdateJob<T>& job, const double* U, int s, int q, double alpha, const double* lam,
+           double* norm_part) {
+  const bool timed = c.prof.on && sizeof(T) == 8;
+  if (timed) c.prof.kmark();
+  const int parts = launch_update<T>(c.A.n, job, U, s, q, alpha, lam, norm_part, c.max_ctas, c.st);
+  if (timed) {
+    c.prof.kmark();
+    c.prof.kflops += 2.0 * (double)c.A.n * s * q * job.nprod;
+  }
+  return parts;
+}
+
 template <class T>
 void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
   if (p <= 0) return;
@@ -318,7 +359,7 @@ void right_multiply(lobpcg_ctx& c, T* W, int ld, int p, const double* Tm) {
   job.out[0] = W;
   job.ld_out[0] = ld;
   job.nprod = 1;
-  launch_update<T>(c.A.n, job, Tm, p, p, 1.0, nullptr, nullptr, c.max_ctas, c.st);
+  update<T>(c, job, Tm, p, p, 1.0, nullptr, nullptr);
 }
 
 // Algorithm 2: W (n x p) <- ortho(W).  Host-driven loop, one flag read per pass.
@@ -373,7 +414,7 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
       job.base[0] = W;
       job.ld_base[0] = ld;
       job.nprod = 1;
-      launch_update<T>(c.A.n, job, c.C, q, p, -1.0, nullptr, nullptr, c.max_ctas, c.st);  // W -= Y C
+      update<T>(c, job, c.C, q, p, -1.0, nullptr, nullptr);  // W -= Y C
     }
     ortho<T>(c, W, ld, p, tau, cap);
     ++passes;
@@ -410,7 +451,7 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
         job.out[0] = W;
         job.ld_out[0] = ld;
         job.nprod = 1;
-        launch_update<T>(c.A.n, job, c.Tm, p, k2, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // W <- W S
+        update<T>(c, job, c.Tm, p, k2, 1.0, nullptr, nullptr);  // W <- W S
       }
       c.stats.w_dropped += p - k2;
     }
@@ -474,7 +515,8 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   ortho<T>(c, b.X[0], ld, m, tau, cap);                                 // X0 <- ortho(X0)
   apply_A<T>(c, b.X[0], ld, m, b.AX[0], ld);                            // AX = A X
   gram<T>(c, cols1<T>(b.X[0], ld, m), cols1<T>(b.AX[0], ld, m), true, c.G);  // a = X^T AX
-  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4);  // a u = u lambda
+  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4,
+              sizeof(T) == 4 ? 1e-10 : 1e-15);  // a u = u lambda
   LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
   {
     UpdateJob<T> job{};
@@ -483,7 +525,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     job.out[0] = b.X[1], job.out[1] = b.AX[1];
     job.ld_out[0] = job.ld_out[1] = ld;
     job.nprod = 2;
-    const int parts = launch_update<T>(n, job, c.U, m, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);
+    const int parts = update<T>(c, job, c.U, m, m, 1.0, c.lam, c.npart);
     launch_lock_and_p(m, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.colmax, c.up,
                       false, c.st);
   }
@@ -537,9 +579,9 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     c.prof.mark(PH_RR_GRAM);
     gram<T>(c, V, AV, true, c.G);                                       // a = V^T AV (upper)
     c.prof.mark(PH_RR_EIG);
-    // Rayleigh-Ritz; the FP32 phase, whose Ritz vectors go to FP32 blocks, takes the
-    // two-stage solver, the FP64 phase the plain FP64 Jacobi
-    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4);
+    // Rayleigh-Ritz; the FP32 phase, whose Ritz vectors go to FP32 blocks (rounding 6e-8),
+    // takes the two-stage solver stopped at 1e-10 relative, the FP64 phase plain FP64 Jacobi
+    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, sizeof(T) == 4, sizeof(T) == 4 ? 1e-10 : 1e-15);
     c.prof.mark(PH_UPDATE);
     LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
     const int nxt = cur ^ 1;
@@ -548,7 +590,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     job.out[0] = b.X[nxt], job.out[1] = b.AX[nxt];
     job.ld_out[0] = job.ld_out[1] = ld;
     job.nprod = 2;
-    const int parts = launch_update<T>(n, job, c.U, s, m, 1.0, c.lam, c.npart, c.max_ctas, c.st);  // X = V u_x
+    const int parts = update<T>(c, job, c.U, s, m, 1.0, c.lam, c.npart);  // X = V u_x
     launch_lock_and_p(s, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.colmax, c.up,
                       true, c.st);                                      // lock, u_p
     read_lock(m);
@@ -605,7 +647,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
       pj.out[0] = b.P[nxt], pj.out[1] = b.AP[nxt];
       pj.ld_out[0] = pj.ld_out[1] = ld;
       pj.nprod = 2;
-      launch_update<T>(n, pj, c.up, s, pw_new, 1.0, nullptr, nullptr, c.max_ctas, c.st);  // P = V u_p
+      update<T>(c, pj, c.up, s, pw_new, 1.0, nullptr, nullptr);  // P = V u_p
     }
     c.prof.mark(PH_OTHER);
     cur = nxt;
@@ -833,7 +875,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       job.out[0] = Xs;
       job.ld_out[0] = b.ld;
       job.nprod = 1;
-      launch_update<double>(n, job, c->S, k, k, 1.0, nullptr, nullptr, c->max_ctas, c->st);
+      update<double>(*c, job, c->S, k, k, 1.0, nullptr, nullptr);
     }
     apply_A<double>(*c, Xs, b.ld, k, AXs, b.ld);
     c->stats.spmm_columns -= k;  // the check product is not part of the iteration
@@ -850,7 +892,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       job.out[0] = b.W, job.out[1] = b.AW;
       job.ld_out[0] = job.ld_out[1] = b.ld;
       job.nprod = 2;
-      const int parts = launch_update<double>(n, job, c->Tm, k, k, 1.0, c->lam, c->npart, c->max_ctas, c->st);
+      const int parts = update<double>(*c, job, c->Tm, k, k, 1.0, c->lam, c->npart);
       LockState tmp{0, k, 0, 0, 0, 0};
       LB_CUDA(cudaMemcpyAsync(c->lock, &tmp, sizeof tmp, cudaMemcpyHostToDevice, c->st));
       launch_lock_and_p(k, k, k, n, c->npart, parts, c->Tm, tol, 0, tau, c->lock, c->resnorm, c->colmax, c->up, false, c->st);
@@ -885,6 +927,9 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->kernel_launches = launch_counter() - launches0;
       info->spmm_launches = c->stats.spmm_launches;
       info->precond_fallback = c->stats.precond_fallback;
+      info->update_fp64_seconds = c->prof.on ? c->prof.kseconds() : 0.0;
+      info->update_fp64_flops = c->prof.on ? c->prof.kflops : 0.0;
+      info->update_fp64_launches = c->prof.on ? (int64_t)(c->prof.kused / 2) : 0;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))
