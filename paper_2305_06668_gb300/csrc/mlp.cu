@@ -193,6 +193,35 @@ __global__ void adam_kernel(int np, float* __restrict__ P, float* __restrict__ g
 }  // namespace
 
 // ---- learned preconditioner step inside the solver ----------------------------------------
+// Two passes.  The diagonal step w = r / guard(d - theta) over every (row, column) is a
+// light elementwise kernel; the MLP scale applies only where |d - theta| <= 64 c, a few
+// rows around each Ritz value, and its register-heavy forward pass runs in a second
+// kernel that recomputes those entries (the same expression, so the result is the same as
+// one fused pass).
+template <class T>
+__global__ void __launch_bounds__(256) precond_diag_kernel(int64_t n, const T* __restrict__ X,
+                                                           const T* __restrict__ AX, int ld,
+                                                           const double* __restrict__ lam, int c0, int a,
+                                                           const double* __restrict__ diag, T* __restrict__ W,
+                                                           int ldw) {
+  // 2-D walk (row, column) without 64-bit divisions: a_pad = pow2 >= a lanes per row
+  const int a_pad = a <= 1 ? 1 : (a <= 2 ? 2 : (a <= 4 ? 4 : (a <= 8 ? 8 : (a <= 16 ? 16 : 32))));
+  const int rows_per_block = blockDim.x / a_pad;
+  const int j = threadIdx.x % a_pad;
+  const int rl = threadIdx.x / a_pad;
+  if (j >= a) return;
+  const double l = lam[c0 + j];
+  const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
+  const T lt = (T)l;
+  for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rl; i < n; i += (int64_t)gridDim.x * rows_per_block) {
+    const T r = AX[i * ld + c0 + j] - lt * X[i * ld + c0 + j];
+    // in the block's precision: exact for FP64, and the FP64 units stay free in the FP32 phase
+    T delta = (T)diag[i] - lt;
+    if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
+    W[i * ldw + j] = r * T(1) / delta;
+  }
+}
+
 template <class T>
 __global__ void precond_learned_kernel(int64_t n, const T* __restrict__ X, const T* __restrict__ AX, int ld,
                                        const double* __restrict__ lam, int c0, int a, const double* __restrict__ diag,
@@ -201,28 +230,23 @@ __global__ void precond_learned_kernel(int64_t n, const T* __restrict__ X, const
   __shared__ __align__(16) float sP[kNumParams + 3];
   load_params(P, sP);
   float h1[H];
-  // 2-D walk (row, column) without 64-bit divisions
-  const int a_pad = a <= 1 ? 1 : (a <= 2 ? 2 : (a <= 4 ? 4 : (a <= 8 ? 8 : (a <= 16 ? 16 : 32))));
-  const int rows_per_block = blockDim.x / a_pad;
-  const int j = threadIdx.x % a_pad;
-  const int rl = threadIdx.x / a_pad;
-  if (j >= a) return;
-  const double l = lam[c0 + j];
-  const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
-  const float g = (float)colmax[c0 + j];
-  const T lt = (T)l, band = (T)(64.0 * cscale);
-  for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rl; i < n; i += (int64_t)gridDim.x * rows_per_block) {
-    const T r = AX[i * ld + c0 + j] - lt * X[i * ld + c0 + j];
-    // in the block's precision: exact for FP64, and the FP64 units stay free in the FP32 phase
-    const T dd = (T)diag[i] - lt;
-    T delta = dd;
-    if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
-    T scale = T(1);
-    if (fabs(dd) <= band) {
+  const T band = (T)(64.0 * cscale);
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const T di = (T)diag[i];
+    for (int j = 0; j < a; ++j) {
+      const double l = lam[c0 + j];
+      const T lt = (T)l;
+      const T dd = di - lt;
+      if (!(fabs(dd) <= band)) continue;
+      const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
+      const float g = (float)colmax[c0 + j];
+      const T r = AX[i * ld + c0 + j] - lt * X[i * ld + c0 + j];
+      T delta = dd;
+      if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
       const float f3 = g > 0.f ? (float)r / g : 0.f;
-      scale = (T)softplusf(forward_z(sP, (float)dd / (float)(8.0 * cscale), rho[i] / cscale, f3, h1));
+      const T scale = (T)softplusf(forward_z(sP, (float)dd / (float)(8.0 * cscale), rho[i] / cscale, f3, h1));
+      W[i * ldw + j] = r * scale / delta;
     }
-    W[i * ldw + j] = r * scale / delta;
   }
 }
 
@@ -322,8 +346,10 @@ void launch_precond_learned(int64_t n, const T* X, const T* AX, int ld, const do
                             const double* diag, const float* rho, float cscale, const double* colmax, const float* P,
                             T* W, int ldw, cudaStream_t st) {
   if (n <= 0 || a <= 0) return;
-  precond_learned_kernel<T><<<grid(n * a, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, rho, cscale, colmax, P,
-                                                             W, ldw);
+  precond_diag_kernel<T><<<grid(n * a, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, W, ldw);
+  LB_LAUNCH_CHECK();
+  precond_learned_kernel<T><<<grid(n, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, rho, cscale, colmax, P,
+                                                          W, ldw);
   LB_LAUNCH_CHECK();
 }
 template void launch_precond_learned<double>(int64_t, const double*, const double*, int, const double*, int, int,
