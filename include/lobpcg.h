@@ -220,10 +220,15 @@ LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int 
 LOBPCG_API lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U, lobpcg_stream stream);
 
 /* Same contract, two-stage method (the Rayleigh-Ritz solve of the FP32 phase of the mixed
- * form): FP32 Jacobi, one FP64 Cholesky-QR of its rotation matrix Q, then FP64 Jacobi on
- * Q^T a Q accumulated into Q.  Eigenvalues and residuals to FP64 absolute accuracy
- * (~eps ||a||), U orthonormal to FP64 rounding; exact zero couplings of a are not kept. */
-LOBPCG_API lobpcg_status lobpcg_syev2_f64(int s, const double* a, double* lam, double* U, lobpcg_stream stream);
+ * form): FP32 Jacobi, one FP64 Cholesky-QR of its rotation matrix Q, then Jacobi on
+ * Q^T a Q accumulated into Q until its off-diagonal mass is <= tol ||a||_F.  tol = 0 means
+ * 1e-15: FP64 rotations, eigenvalues and residuals to FP64 absolute accuracy (~eps ||a||),
+ * U orthonormal to FP64 rounding.  1e-12 <= tol < 1e-6 (the solver uses 1e-10): the
+ * rotations of that last stage run in FP32 on the small off-diagonal part and on the
+ * rotation product minus the identity (FP64 diagonal), good to about tol.  Exact zero
+ * couplings of a are not kept.  EINVAL for tol outside [0, 1e-6). */
+LOBPCG_API lobpcg_status lobpcg_syev2_f64(int s, const double* a, double tol, double* lam, double* U,
+                                          lobpcg_stream stream);
 
 /* Algorithm 2 in place on X (n x p row-major, ldx, p <= 32).  stats (host, optional):
  * [0] Cholesky-QR passes, [1] shifted attempts, [2] SVQB steps, [3] cap hit (0/1). */

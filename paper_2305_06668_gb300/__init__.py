@@ -274,16 +274,18 @@ def gram_noalloc(X, Y, out=None, stream=None):
     return Cm.t()
 
 
-def syev(a, two_stage=False, stream=None):
+def syev(a, two_stage=False, tol=0.0, stream=None):
     """Eigenvalues (ascending) and eigenvectors of symmetric a; two_stage selects the
-    FP32-then-FP64 Jacobi used by the FP32 phase of the mixed form."""
+    FP32-then-FP64 Jacobi used by the FP32 phase of the mixed form, stopped at tol (0: 1e-15)."""
     torch = _torch()
     s = a.shape[0]
     ac = a.t().contiguous()  # column-major storage of a
     lam = torch.empty(s, dtype=torch.float64, device=a.device)
     U = torch.empty((s, s), dtype=torch.float64, device=a.device)
-    fn = lib().lobpcg_syev2_f64 if two_stage else lib().lobpcg_syev_f64
-    _check(fn(C.c_int(s), _ptr(ac), _ptr(lam), _ptr(U), _stream(stream)))
+    if two_stage:
+        _check(lib().lobpcg_syev2_f64(C.c_int(s), _ptr(ac), C.c_double(tol), _ptr(lam), _ptr(U), _stream(stream)))
+    else:
+        _check(lib().lobpcg_syev_f64(C.c_int(s), _ptr(ac), _ptr(lam), _ptr(U), _stream(stream)))
     return lam, U.t()
 
 

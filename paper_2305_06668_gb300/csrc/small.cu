@@ -129,6 +129,99 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
   return -1;
 }
 
+// Jacobi polish of a nearly diagonal symmetric matrix a = diag(d) + E, |E| small against
+// ||a||: the rotations run in FP32 on E (ld lde) and on Dl = V - I (ld ldd), the rotation
+// product accumulated so far, while the diagonal d and the rotation parameters stay in
+// FP64.  With rotation angles theta ~ |E| / gap, FP32 adds errors of order 6e-8 |E| to E
+// and 6e-8 theta to Dl.  That is far below the 1e-10 relative accuracy this is used for.
+// Dl must hold zeros on entry.  Stops when off(E) <= rel_tol * fro.  Returns the sweeps
+// done, or -1.
+__device__ int jacobi_polish(int s, double* d, float* E, int lde, float* Dl, int ldd, double* rot, double* red,
+                             double rel_tol, double fro, int max_sweeps) {
+  const int N = s + (s & 1);
+  const int half = N / 2;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double o2 = 0.0;
+    for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+      const int i = e % s, j = e / s;
+      if (i != j) {
+        const double v = E[i + j * lde];
+        o2 += v * v;
+      }
+    }
+    const double off = sqrt(block_sum(o2, red));
+    if (off <= rel_tol * fro || off == 0.0) return sweep;
+    for (int r = 0; r < N - 1; ++r) {
+      // rot[4i .. 4i+3] = p, q, c, s (as doubles; p < 0: skip); the diagonal is updated here
+      for (int i = threadIdx.x; i < half; i += blockDim.x) {
+        int p, q;
+        if (i == 0) p = N - 1, q = r;
+        else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
+        if (p > q) { const int t = p; p = q; q = t; }
+        double c = 1.0, sn = 0.0;
+        bool skip = q >= s;
+        if (!skip) {
+          const double apq = (double)E[p + q * lde];
+          if (apq == 0.0) {
+            skip = true;
+          } else {
+            const double tau = (d[q] - d[p]) / (2.0 * apq);
+            const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+            c = 1.0 / sqrt(1.0 + t * t);
+            sn = t * c;
+            d[p] -= t * apq;
+            d[q] += t * apq;
+          }
+        }
+        rot[4 * i + 0] = skip ? -1.0 : (double)p;
+        rot[4 * i + 1] = (double)q;
+        rot[4 * i + 2] = c;
+        rot[4 * i + 3] = sn;
+      }
+      __syncthreads();
+      // rows p, q of E (entries outside the pair's 2 x 2 block) and columns p, q of Dl
+      for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        if (rot[4 * i] < 0.0) continue;
+        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const double cd = rot[4 * i + 2], sd = rot[4 * i + 3];
+        const float c = (float)cd, sn = (float)sd;
+        if (j != p && j != q) {
+          const float epj = E[p + j * lde], eqj = E[q + j * lde];
+          E[p + j * lde] = c * epj - sn * eqj;
+          E[q + j * lde] = sn * epj + c * eqj;
+        }
+        // V' = V J with V = I + Dl
+        const float cm1 = (float)(-sd * sd / (1.0 + cd));  // c - 1 without cancellation
+        const float djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
+        float np = c * djp - sn * djq, nq = sn * djp + c * djq;
+        if (j == p) np += cm1, nq += sn;
+        if (j == q) np -= sn, nq += cm1;
+        Dl[j + p * ldd] = np;
+        Dl[j + q * ldd] = nq;
+      }
+      __syncthreads();
+      // columns p, q of E; the pair's own off-diagonal entry is annihilated
+      for (int e = threadIdx.x; e < half * s; e += blockDim.x) {
+        const int i = e / s, j = e % s;
+        if (rot[4 * i] < 0.0) continue;
+        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const float c = (float)rot[4 * i + 2], sn = (float)rot[4 * i + 3];
+        if (j == p || j == q) {
+          if (j == p) E[q + p * lde] = 0.f;
+          else E[p + q * lde] = 0.f;
+          continue;
+        }
+        const float ejp = E[j + p * lde], ejq = E[j + q * lde];
+        E[j + p * lde] = c * ejp - sn * ejq;
+        E[j + q * lde] = sn * ejp + c * ejq;
+      }
+      __syncthreads();
+    }
+  }
+  return -1;
+}
+
 __device__ int jacobi_cta(int s, double* a, int lda, double* V, int ldv, double* rot, double* red) {
   return jacobi_sweeps<double>(s, a, lda, V, ldv, rot, red, 1e-15, 40, true);
 }
@@ -157,6 +250,7 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
   __shared__ double red[32];
   __shared__ double rot[4 * (kMaxS / 2 + 1)];
   __shared__ int rank[kMaxS];
+  __shared__ double dsh[kMaxS];
   __shared__ int flag;
   const int ld = s + 1;  // odd stride against bank conflicts
   double* A = sm;
@@ -224,6 +318,43 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
       }
     }
     __syncthreads();
+    if (tol64 >= 1e-12) {
+      // ---- polish to tol64 with FP32 rotations on the small off-diagonal part (E) and on
+      // the rotation product minus the identity (Dl); U = Q (I + Dl) at the end
+      float* E = reinterpret_cast<float*>(C);
+      float* Dl = E + s * ld;
+      double f2 = 0.0;
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int i = e % s, j = e / s;
+        const double v = A[i + j * ld];
+        f2 += v * v;
+        E[i + j * ld] = i == j ? 0.f : (float)v;
+        Dl[i + j * ld] = 0.f;
+        if (i == j) dsh[i] = v;
+      }
+      const double fro = sqrt(block_sum(f2, red));
+      sw = jacobi_polish(s, dsh, E, ld, Dl, ld, rot, red, tol64, fro, 20);
+      __syncthreads();
+      for (int i = threadIdx.x; i < s; i += blockDim.x) {
+        const double li = dsh[i];
+        int r = 0;
+        for (int j = 0; j < s; ++j) {
+          const double lj = dsh[j];
+          r += (lj < li) || (lj == li && j < i);
+        }
+        rank[i] = r;
+        lam[r] = li;
+      }
+      __syncthreads();
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
+        const int r = e % s, i = e / s;
+        double acc = B[r + i * ld];
+        for (int t = 0; t < s; ++t) acc += B[r + t * ld] * (double)Dl[t + i * ld];
+        U[r + rank[i] * s] = acc;
+      }
+      if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
+      return;
+    }
     // ---- FP64 pass, rotations accumulated into Q
     sw = jacobi_sweeps<double>(s, A, ld, B, ld, rot, red, tol64, 40, false);
   }

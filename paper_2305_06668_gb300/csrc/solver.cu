@@ -1066,12 +1066,13 @@ extern "C" lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, do
   });
 }
 
-extern "C" lobpcg_status lobpcg_syev2_f64(int s, const double* a, double* lam, double* U,
+extern "C" lobpcg_status lobpcg_syev2_f64(int s, const double* a, double tol, double* lam, double* U,
                                           lobpcg_stream stream) {
   return guarded(nullptr, [&]() -> lobpcg_status {
     require(s >= 1 && s <= kMaxS && a && lam && U, "lobpcg_syev2_f64: need 1 <= s <= 96 and non-NULL arrays");
+    require(tol >= 0.0 && tol < 1e-6, "lobpcg_syev2_f64: need 0 <= tol < 1e-6");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    launch_syev(s, a, false, lam, U, nullptr, st, true);
+    launch_syev(s, a, false, lam, U, nullptr, st, true, tol > 0.0 ? tol : 1e-15);
     LB_CUDA(cudaStreamSynchronize(st));
     return LOBPCG_OK;
   });

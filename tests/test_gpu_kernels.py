@@ -176,3 +176,26 @@ def test_syev_clustered_and_repeated_eigenvalues(s, two_stage):
     assert np.max(np.abs(lg - lam)) <= 1e-13 * nrm
     assert np.max(np.abs(U.T @ U - np.eye(s))) <= 1e-13 * s
     assert np.max(np.abs(a @ U - U * lg)) <= 1e-13 * nrm
+
+
+@pytest.mark.parametrize("s", [3, 21, 63, 96])
+def test_syev_two_stage_fp32_polish(s):
+    """Two-stage solve stopped at 1e-10 (FP32 rotations in its last stage), as the FP32
+    phase of the mixed form runs it, on a graded spectrum with a cluster: eigenvalues and
+    residuals to 1e-9 ||a||, U orthonormal to 1e-9."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    g = np.random.default_rng(2000 + s)
+    lam = np.sort(np.concatenate([g.uniform(0.0, 0.05, s // 3), g.uniform(0.05, 20.0, s - s // 3)]))
+    if s > 6:
+        lam[2:5] = lam[2] + np.array([0.0, 1e-9, 3e-9])
+    lam = np.sort(lam)
+    Q, _ = np.linalg.qr(g.standard_normal((s, s)))
+    a = (Q * lam) @ Q.T
+    a = 0.5 * (a + a.T)
+    lg, U = lb.syev(torch.from_numpy(a).cuda(), two_stage=True, tol=1e-10)
+    lg, U = lg.cpu().numpy(), U.cpu().numpy()
+    nrm = max(1.0, np.linalg.norm(a))
+    assert np.max(np.abs(lg - lam)) <= 1e-9 * nrm
+    assert np.max(np.abs(U.T @ U - np.eye(s))) <= 1e-9
+    assert np.max(np.abs(a @ U - U * lg)) <= 1e-9 * nrm
