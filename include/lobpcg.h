@@ -224,8 +224,8 @@ LOBPCG_API lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, do
  * Q^T a Q accumulated into Q until its off-diagonal mass is <= tol ||a||_F.  tol = 0 means
  * 1e-15: FP64 rotations, eigenvalues and residuals to FP64 absolute accuracy (~eps ||a||),
  * U orthonormal to FP64 rounding.  1e-12 <= tol < 1e-6 (the solver uses 1e-10): the
- * rotations of that last stage run in FP32 on the small off-diagonal part and on the
- * rotation product minus the identity (FP64 diagonal), good to about tol.  Exact zero
+ * rotations of that last stage update the small off-diagonal part in FP32 (diagonal and
+ * rotation product in FP64), good to about tol.  Exact zero
  * couplings of a are not kept.  EINVAL for tol outside [0, 1e-6). */
 LOBPCG_API lobpcg_status lobpcg_syev2_f64(int s, const double* a, double tol, double* lam, double* U,
                                           lobpcg_stream stream);

@@ -130,13 +130,12 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
 }
 
 // Jacobi polish of a nearly diagonal symmetric matrix a = diag(d) + E, |E| small against
-// ||a||: the rotations run in FP32 on E (ld lde) and on Dl = V - I (ld ldd), the rotation
-// product accumulated so far, while the diagonal d and the rotation parameters stay in
-// FP64.  With rotation angles theta ~ |E| / gap, FP32 adds errors of order 6e-8 |E| to E
-// and 6e-8 theta to Dl.  That is far below the 1e-10 relative accuracy this is used for.
-// Dl must hold zeros on entry.  Stops when off(E) <= rel_tol * fro.  Returns the sweeps
-// done, or -1.
-__device__ int jacobi_polish(int s, double* d, float* E, int lde, float* Dl, int ldd, double* rot, double* red,
+// ||a||: the rotations run in FP32 on E (ld lde), which stays small whatever the angle, so
+// FP32 adds errors of order 6e-8 |E| there.  The diagonal d, the rotation parameters and
+// Dl = V - I (ld ldd), the rotation product accumulated so far, stay in FP64.  Dl must be
+// FP64 because the angles inside a cluster of eigenvalues are not small.  Dl must hold
+// zeros on entry.  Stops when off(E) <= rel_tol * fro.  Returns the sweeps done, or -1.
+__device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, int ldd, double* rot, double* red,
                              double rel_tol, double fro, int max_sweeps) {
   const int N = s + (s & 1);
   const int half = N / 2;
@@ -192,11 +191,11 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, float* Dl, int
           E[q + j * lde] = sn * epj + c * eqj;
         }
         // V' = V J with V = I + Dl
-        const float cm1 = (float)(-sd * sd / (1.0 + cd));  // c - 1 without cancellation
-        const float djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
-        float np = c * djp - sn * djq, nq = sn * djp + c * djq;
-        if (j == p) np += cm1, nq += sn;
-        if (j == q) np -= sn, nq += cm1;
+        const double cm1 = -sd * sd / (1.0 + cd);  // c - 1 without cancellation
+        const double djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
+        double np = cd * djp - sd * djq, nq = sd * djp + cd * djq;
+        if (j == p) np += cm1, nq += sd;
+        if (j == q) np -= sd, nq += cm1;
         Dl[j + p * ldd] = np;
         Dl[j + q * ldd] = nq;
       }
@@ -319,20 +318,21 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
     }
     __syncthreads();
     if (tol64 >= 1e-12) {
-      // ---- polish to tol64 with FP32 rotations on the small off-diagonal part (E) and on
-      // the rotation product minus the identity (Dl); U = Q (I + Dl) at the end
+      // ---- polish to tol64 with FP32 rotations on the small off-diagonal part (E); the
+      // rotation product minus the identity (Dl) in FP64; U = Q (I + Dl) at the end
       float* E = reinterpret_cast<float*>(C);
-      float* Dl = E + s * ld;
+      double* Dl = A;  // A is read into d and E first
       double f2 = 0.0;
       for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
         const int i = e % s, j = e / s;
         const double v = A[i + j * ld];
         f2 += v * v;
         E[i + j * ld] = i == j ? 0.f : (float)v;
-        Dl[i + j * ld] = 0.f;
         if (i == j) dsh[i] = v;
       }
-      const double fro = sqrt(block_sum(f2, red));
+      const double fro = sqrt(block_sum(f2, red));  // ends with a barrier: A fully read
+      for (int e = threadIdx.x; e < s * s; e += blockDim.x) Dl[(e % s) + (e / s) * ld] = 0.0;
+      __syncthreads();
       sw = jacobi_polish(s, dsh, E, ld, Dl, ld, rot, red, tol64, fro, 20);
       __syncthreads();
       for (int i = threadIdx.x; i < s; i += blockDim.x) {
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(kSmallThreads) syev_kernel(int s, const double
       for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
         const int r = e % s, i = e / s;
         double acc = B[r + i * ld];
-        for (int t = 0; t < s; ++t) acc += B[r + t * ld] * (double)Dl[t + i * ld];
+        for (int t = 0; t < s; ++t) acc += B[r + t * ld] * Dl[t + i * ld];
         U[r + rank[i] * s] = acc;
       }
       if (threadIdx.x == 0 && sweeps_out) *sweeps_out = sw;
