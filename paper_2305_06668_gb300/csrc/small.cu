@@ -155,7 +155,7 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // rot[4i .. 4i+3] = p, q, c, s (as doubles; p < 0: skip); the diagonal is updated here
+      // rot[4i .. 4i+3] = 128 p + q (< 0: skip), c - 1, c, s; the diagonal is updated here
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
         if (i == 0) p = N - 1, q = r;
@@ -176,8 +176,8 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
             d[q] += t * apq;
           }
         }
-        rot[4 * i + 0] = skip ? -1.0 : (double)p;
-        rot[4 * i + 1] = (double)q;
+        rot[4 * i + 0] = skip ? -1.0 : (double)(p * 128 + q);
+        rot[4 * i + 1] = -sn * sn / (1.0 + c);  // c - 1 without cancellation, once per pair
         rot[4 * i + 2] = c;
         rot[4 * i + 3] = sn;
       }
@@ -186,7 +186,7 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
       for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
         const int i = e >> sh, j = e & (sp - 1);
         if (j >= s || rot[4 * i] < 0.0) continue;
-        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const int pq = (int)rot[4 * i], p = pq >> 7, q = pq & 127;
         const double cd = rot[4 * i + 2], sd = rot[4 * i + 3];
         const float c = (float)cd, sn = (float)sd;
         if (j != p && j != q) {
@@ -195,7 +195,7 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
           E[q + j * lde] = sn * epj + c * eqj;
         }
         // V' = V J with V = I + Dl
-        const double cm1 = -sd * sd / (1.0 + cd);  // c - 1 without cancellation
+        const double cm1 = rot[4 * i + 1];
         const double djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
         double np = cd * djp - sd * djq, nq = sd * djp + cd * djq;
         if (j == p) np += cm1, nq += sd;
@@ -208,7 +208,7 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
       for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
         const int i = e >> sh, j = e & (sp - 1);
         if (j >= s || rot[4 * i] < 0.0) continue;
-        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
+        const int pq = (int)rot[4 * i], p = pq >> 7, q = pq & 127;
         const float c = (float)rot[4 * i + 2], sn = (float)rot[4 * i + 3];
         if (j == p || j == q) {
           if (j == p) E[q + p * lde] = 0.f;
