@@ -199,3 +199,54 @@ def test_syev_two_stage_fp32_polish(s):
     assert np.max(np.abs(lg - lam)) <= 1e-9 * nrm
     assert np.max(np.abs(U.T @ U - np.eye(s))) <= 1e-9
     assert np.max(np.abs(a @ U - U * lg)) <= 1e-9 * nrm
+
+
+def test_spmm_csr_f32_split_empty_rows_and_heavy_rows():
+    """Split FP32 product on a CI-like matrix where every 7th row (and column) is empty, a
+    few rows carry many long-range entries and a block of rows carries a dense band (its
+    64-row sub-blocks exceed the shared-memory staging cap and are read from global
+    memory): empty rows give zero rows of Y, long rows are summed in full."""
+    torch = cuda()
+    import scipy.sparse as sp
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=30_011, seed=77)
+    m = a.to_scipy().tolil()
+    keep = np.ones(a.n, dtype=bool)
+    keep[::7] = False
+    g = np.random.default_rng(5)
+    heavy = g.choice(np.flatnonzero(keep), 5, replace=False)
+    for r in heavy:  # 150 long-range partners each, mirrored
+        cols = g.choice(np.flatnonzero(keep), 150, replace=False)
+        v = g.normal(0, 0.005, 150)
+        for c, x in zip(cols, v):
+            if c != r:
+                m[r, c] = x
+                m[c, r] = x
+    for r in range(8001, 8129):  # a dense band block: sub-blocks larger than the staging cap
+        cols = r + g.choice(np.arange(-200, 201), 60, replace=False)
+        for c in cols:
+            if c != r:
+                x = g.normal(0, 0.005)
+                m[r, c] = x
+                m[c, r] = x
+    m = m.tocsr()
+    D = sp.diags(keep.astype(float))
+    m = (D @ m @ D).tocsr()
+    m.sort_indices()
+    m.eliminate_zeros()
+    b = synth.CSR(a.n, m.indptr.astype(np.int64), m.indices.astype(np.int32), m.data.astype(np.float64),
+                  m.diagonal().astype(np.float64))
+    assert np.count_nonzero(np.diff(b.row_ptr) == 0) >= a.n // 7
+    p = 21
+    X = synth.gaussian_block(b.n, p, seed=8)
+    t = lb.upload_csr(b)
+    Y, used = lb.spmm_csr_f32(t["row_ptr"], t["col_idx"], t["val"], _f32_block(torch, X, 24), band=-1)
+    Y = Y.cpu().numpy().astype(np.float64)
+    b32 = synth.CSR(b.n, b.row_ptr, b.col_idx, b.val.astype(np.float32).astype(np.float64), b.diag)
+    X32 = X.astype(np.float32).astype(np.float64)
+    ref = oracle.apply(b32, X32)
+    scale = np.abs(b32.to_scipy()) @ np.abs(X32)
+    nz = int(np.max(np.diff(b.row_ptr))) + 2
+    assert used >= 0
+    assert np.all(Y[~keep] == 0.0)
+    assert np.all(np.abs(Y - ref) <= nz * np.finfo(np.float32).eps * scale + 1e-30)
