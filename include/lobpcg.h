@@ -214,6 +214,16 @@ LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64
 LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int ldx, int q, const double* Y,
                               int ldy, double* C, lobpcg_stream stream);
 
+/* C = X^T Y for FP32 blocks, the Gram of the mixed form (Algorithm 1's projected matrices
+ * with FP32 storage).  X: n x p float (ldx), Y: n x q float (ldy), p, q <= 96.  C: device,
+ * FP64, column-major p x q.  When the rows are 16-byte aligned with ldx == ldy a multiple
+ * of 4, it runs on the tensor cores: TF32 mma with the 3xTF32 split, x = x_hi + x_lo and
+ * a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, which keeps ~21 bits per product.  Otherwise it
+ * runs on the FP32 FMA units.  Sums are FP32 within a CTA, FP64 across CTAs (fixed
+ * order). */
+LOBPCG_API lobpcg_status lobpcg_gram_f32(int64_t n, int p, const float* X, int ldx, int q, const float* Y,
+                              int ldy, double* C, lobpcg_stream stream);
+
 /* Symmetric eigen-decomposition of s x s column-major a (s <= 96) by parallel-order
  * Jacobi rotations in FP64 (the Rayleigh-Ritz solve of Algorithm 1).  lam: device, s
  * values ascending; U: device, column-major s x s eigenvectors. */

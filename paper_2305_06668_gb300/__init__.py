@@ -71,7 +71,7 @@ def lib():
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
-                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64"):
+                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -255,6 +255,19 @@ def gram(X, Y, stream=None):
     q = Y.shape[1]
     Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)  # column-major p x q
     _check(lib().lobpcg_gram_f64(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
+                                 C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
+    return Cm.t()
+
+
+def gram_f32(X, Y, stream=None):
+    """C = X^T Y (FP64 result) for float32 row-major blocks X (n x p), Y (n x q)."""
+    torch = _torch()
+    n, p = X.shape
+    q = Y.shape[1]
+    if X.dtype != torch.float32 or Y.dtype != torch.float32:
+        raise TypeError("gram_f32: X and Y must be float32")
+    Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)
+    _check(lib().lobpcg_gram_f32(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
                                  C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
     return Cm.t()
 

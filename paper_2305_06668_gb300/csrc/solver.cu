@@ -1055,6 +1055,19 @@ extern "C" lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int 
   });
 }
 
+extern "C" lobpcg_status lobpcg_gram_f32(int64_t n, int p, const float* X, int ldx, int q, const float* Y,
+                                         int ldy, double* C, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && X && Y && C, "lobpcg_gram_f32: NULL argument or n < 1");
+    require(p >= 1 && q >= 1 && p <= kMaxS && q <= kMaxS && ldx >= p && ldy >= q,
+            "lobpcg_gram_f32: need 1 <= p, q <= 96, ld >= width");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    gram<float>(s.c, cols1<float>(X, ldx, p), cols1<float>(Y, ldy, q), false, C);
+    s.c.sync();
+    return LOBPCG_OK;
+  });
+}
+
 extern "C" lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U,
                                          lobpcg_stream stream) {
   return guarded(nullptr, [&]() -> lobpcg_status {

@@ -8,6 +8,7 @@
 // multi-stage shared-memory ring (row stride ld + VEC to spread banks), so the loads
 // of chunk k+S-1 overlap the arithmetic on chunk k.
 #include <algorithm>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -161,6 +162,180 @@ __global__ void __launch_bounds__(256) gram_pipe_kernel(int64_t n, Cols<T> A, Co
     const int i = tile_i[tt] * TI + ij / TJ, j = tile_j[tt] * TJ + ij % TJ;
     if (i < pa && j < pb && (!upper || i <= j)) out[i + j * pa] = scratch[e];
   }
+}
+
+// ------------------------------------------------------------------ Gram, tensor cores
+// FP32 Gram C = A^T B on the tensor cores (mma.sync m16n8k8, TF32 inputs, FP32
+// accumulation) with the 3xTF32 split: x = x_hi + x_lo, both TF32, and
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, so each product keeps about 21 bits: FP32-level
+// accuracy for the mixed form.  Rows are staged as in gram_pipe_kernel; a warp owns up to
+// BPW output blocks of 16 x 32 (one M tile, four N tiles) and, when there are fewer blocks
+// than warps, a share of the 8-row k steps of every chunk.  The groups of warps that split
+// the k steps are summed in a fixed order.
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(hi) : "f"(x));
+  const float r = x - __uint_as_float(hi);
+  asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(lo) : "f"(r));
+}
+__device__ __forceinline__ void mma_tf32(float* d, const unsigned* a, const unsigned* b) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+      "{%0, %1, %2, %3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// Shared-memory row stride for the tensor-core Gram: >= ld, a multiple of 4 floats, and
+// 8 (mod 32) floats, so the 4 k-rows x 8 columns of a fragment load hit 32 banks.
+__host__ __device__ __forceinline__ int tc_lds(int ld) {
+  int lds = (ld + 3) / 4 * 4;
+  while (lds % 32 != 8) lds += 4;
+  return lds;
+}
+
+template <int R, int S, int BPW>
+__global__ void __launch_bounds__(256) gram_tc_kernel(int64_t n, Cols<float> A, Cols<float> B, int ld, int upper,
+                                                      int mt, int nbk, int kgroups, double* __restrict__ part,
+                                                      int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lds = tc_lds(ld);
+  const int stageA = A.nseg * R * lds, stageB = B.nseg * R * lds;
+  const int stage = stageA + stageB;
+  float* ring = reinterpret_cast<float*>(smem_raw);
+  const int pa = A.width(), pb = B.width();
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int gid = lane >> 2, t4 = lane & 3;
+  const int nblocks = mt * nbk;
+  const int used = nblocks < 8 ? nblocks * kgroups : 8;  // warps with work
+  const bool active = wid < used;
+  const int kg = nblocks < 8 ? wid / nblocks : 0;
+  // fragment offsets (within one stage) of the rows / columns this lane reads; -1: zero
+  int offA[BPW][2], offB[BPW][4];
+  int blk[BPW];
+#pragma unroll
+  for (int b = 0; b < BPW; ++b) {
+    blk[b] = nblocks < 8 ? (wid % nblocks) : wid + 8 * b;
+    const bool ok = active && blk[b] < nblocks && (nblocks < 8 ? b == 0 : true);
+    const int mi = ok ? blk[b] / nbk : 0, nj = ok ? blk[b] % nbk : 0;
+    offA[b][0] = ok ? col_offset(A, mi * 16 + gid, R, lds) : -1;
+    offA[b][1] = ok ? col_offset(A, mi * 16 + gid + 8, R, lds) : -1;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) offB[b][t] = ok ? col_offset(B, nj * 32 + t * 8 + gid, R, lds) : -1;
+    if (!ok) blk[b] = -1;
+  }
+  float acc[BPW][4][4];
+#pragma unroll
+  for (int b = 0; b < BPW; ++b)
+#pragma unroll
+    for (int t = 0; t < 4; ++t)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[b][t][e] = 0.f;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  const int nchunks = (int)((r_end - r_begin + R - 1) / R);
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if (k < nchunks) {
+      issue_chunk<float, R>(A, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage);
+      issue_chunk<float, R>(B, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage + stageA);
+    }
+    cp_async_commit();
+  }
+  for (int k = 0; k < nchunks; ++k) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    {
+      const int kn = k + S - 1;
+      if (kn < nchunks) {
+        float* dst = ring + (kn % S) * stage;
+        issue_chunk<float, R>(A, ld, lds, r_begin + (int64_t)kn * R, r_end, dst);
+        issue_chunk<float, R>(B, ld, lds, r_begin + (int64_t)kn * R, r_end, dst + stageA);
+      }
+      cp_async_commit();
+    }
+    if (active) {
+      const float* sa = ring + (k % S) * stage;
+      const float* sb = sa + stageA;
+      for (int st = kg; st < R / 8; st += kgroups) {
+        const int r0 = st * 8 + t4, r1 = r0 + 4;
+#pragma unroll
+        for (int b = 0; b < BPW; ++b) {
+          if (blk[b] < 0) continue;
+          unsigned ah[4], al[4];
+          split_tf32(offA[b][0] >= 0 ? sa[offA[b][0] + r0 * lds] : 0.f, ah[0], al[0]);
+          split_tf32(offA[b][1] >= 0 ? sa[offA[b][1] + r0 * lds] : 0.f, ah[1], al[1]);
+          split_tf32(offA[b][0] >= 0 ? sa[offA[b][0] + r1 * lds] : 0.f, ah[2], al[2]);
+          split_tf32(offA[b][1] >= 0 ? sa[offA[b][1] + r1 * lds] : 0.f, ah[3], al[3]);
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            unsigned bh[2], bl[2];
+            split_tf32(offB[b][t] >= 0 ? sb[offB[b][t] + r0 * lds] : 0.f, bh[0], bl[0]);
+            split_tf32(offB[b][t] >= 0 ? sb[offB[b][t] + r1 * lds] : 0.f, bh[1], bl[1]);
+            mma_tf32(acc[b][t], ah, bh);
+            mma_tf32(acc[b][t], ah, bl);
+            mma_tf32(acc[b][t], al, bh);
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  // sum the k groups in order into an (mt*16) x (nbk*32) FP64 scratch (reusing the ring)
+  double* scratch = reinterpret_cast<double*>(smem_raw);
+  const int SM = mt * 16, SN = nbk * 32;
+  for (int e = threadIdx.x; e < SM * SN; e += blockDim.x) scratch[e] = 0.0;
+  __syncthreads();
+  for (int g = 0; g < (nblocks < 8 ? kgroups : 1); ++g) {
+    if (active && kg == g) {
+#pragma unroll
+      for (int b = 0; b < BPW; ++b) {
+        if (blk[b] < 0) continue;
+        const int mi = blk[b] / nbk, nj = blk[b] % nbk;
+#pragma unroll
+        for (int t = 0; t < 4; ++t)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int i = mi * 16 + gid + (e >> 1) * 8;
+            const int j = nj * 32 + t * 8 + 2 * t4 + (e & 1);
+            scratch[i + j * SM] += (double)acc[b][t][e];
+          }
+      }
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.x * pa * pb;
+  for (int e = threadIdx.x; e < pa * pb; e += blockDim.x) {
+    const int i = e % pa, j = e / pa;
+    if (!upper || i <= j) out[i + j * pa] = scratch[i + j * SM];
+  }
+}
+
+template <int R, int S, int BPW>
+int gram_tc_launch(int64_t n, const Cols<float>& a, const Cols<float>& b, int ld, bool upper, double* part,
+                   int max_ctas, cudaStream_t st) {
+  const int pa = a.width(), pb = b.width();
+  const int mt = (pa + 15) / 16, nbk = (pb + 31) / 32;
+  const int nblocks = mt * nbk;
+  const int kgroups = nblocks < 8 ? std::min(8 / nblocks, R / 8) : 1;
+  const int lds = tc_lds(ld);
+  const size_t ring = (size_t)S * (a.nseg + b.nseg) * R * lds * sizeof(float);
+  const size_t scr = (size_t)mt * 16 * nbk * 32 * sizeof(double);
+  const size_t smem = std::max(ring, scr);
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(gram_tc_kernel<R, S, BPW>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    return true;
+  }();
+  (void)attr;
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  gram_tc_kernel<R, S, BPW><<<(unsigned)ctas, 256, smem, st>>>(n, a, b, ld, upper ? 1 : 0, mt, nbk, kgroups, part,
+                                                               rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
 }
 
 // ------------------------------------------------------------------------ update
@@ -479,6 +654,16 @@ int gram_partials_pipe(int64_t n, const Cols<T>& a, const Cols<T>& b, bool upper
   const int pa = a.width(), pb = b.width();
   const size_t ring_per_stage = (size_t)(a.nseg + b.nseg) * 32 * padded_ld<T>(ld) * sizeof(T);
   if (ring_per_stage * 2 > 190 * 1024) return 0;
+  if constexpr (std::is_same<T, float>::value) {
+    // tensor cores (3xTF32) when the blocks fit: ring <= 200 KB at 64 rows x 2 stages
+    const size_t tc_ring = (size_t)2 * (a.nseg + b.nseg) * 64 * tc_lds(ld) * sizeof(float);
+    const int nblocks = ((pa + 15) / 16) * ((pb + 31) / 32);
+    if (pa <= kMaxS && pb <= kMaxS && tc_ring <= 190 * 1024 && nblocks <= 24) {
+      if (nblocks <= 8) return gram_tc_launch<64, 2, 1>(n, a, b, ld, upper, part, max_ctas, st);
+      if (nblocks <= 16) return gram_tc_launch<64, 2, 2>(n, a, b, ld, upper, part, max_ctas, st);
+      return gram_tc_launch<64, 2, 3>(n, a, b, ld, upper, part, max_ctas, st);
+    }
+  }
   if (sizeof(T) == 4 && pa >= 16 && pb >= 16 && count_tiles(pa, pb, 8, 8, upper) <= 256) {
     // long stages: enough rows per thread group between barriers
     const size_t stage128 = (size_t)(a.nseg + b.nseg) * 128 * padded_ld<T>(ld) * sizeof(T);

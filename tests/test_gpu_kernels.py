@@ -250,3 +250,25 @@ def test_spmm_csr_f32_split_empty_rows_and_heavy_rows():
     assert used >= 0
     assert np.all(Y[~keep] == 0.0)
     assert np.all(np.abs(Y - ref) <= nz * np.finfo(np.float32).eps * scale + 1e-30)
+
+
+@pytest.mark.parametrize("n,p,q,ld", [(1, 1, 1, 4), (97, 5, 3, 8), (10_007, 21, 21, 24), (100_003, 63, 63, 64),
+                                      (50_001, 42, 21, 44), (4_099, 96, 40, 96), (20_011, 16, 16, 17)])
+def test_gram_f32_matches_oracle(n, p, q, ld):
+    """FP32 Gram (tensor-core 3xTF32 path when ld is a multiple of 4, FP32 FMA otherwise)
+    against the FP64 oracle on the FP32-rounded blocks: |C - ref| <= 2^-19 |X|^T |Y| + a
+    term for the FP32 sums over the rows of one CTA."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    X = synth.gaussian_block(n, p, seed=11).astype(np.float32).astype(np.float64)
+    Y = synth.gaussian_block(n, q, seed=12).astype(np.float32).astype(np.float64)
+    def dev32(M):
+        buf = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+        buf[:, :M.shape[1]] = torch.from_numpy(M.astype(np.float32)).cuda()
+        return buf[:, :M.shape[1]]
+    Cg = lb.gram_f32(dev32(X), dev32(Y)).cpu().numpy()
+    ref = oracle.gram(X, Y)
+    scale = np.abs(X).T @ np.abs(Y)
+    rows_per_cta = max(64, n // 304 + 64)
+    tol = (2.0 ** -19 + rows_per_cta * np.finfo(np.float32).eps) * scale + 1e-30
+    assert np.all(np.abs(Cg - ref) <= tol)
