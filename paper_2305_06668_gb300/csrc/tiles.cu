@@ -168,7 +168,8 @@ __global__ void __launch_bounds__(256) gram_pipe_kernel(int64_t n, Cols<T> A, Co
 // FP32 Gram C = A^T B on the tensor cores (mma.sync m16n8k8, TF32 inputs, FP32
 // accumulation) with the 3xTF32 split: x = x_hi + x_lo, both TF32, and
 // a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, so each product keeps about 21 bits: FP32-level
-// accuracy for the mixed form.  Rows are staged as in gram_pipe_kernel; a warp owns up to
+// accuracy for the mixed form.  Each 8-row step is summed by the tensor core from zero and
+// added to the running FP32 sums with ordinary round-to-nearest adds.  Rows are staged as in gram_pipe_kernel; a warp owns up to
 // BPW output blocks of 16 x 32 (one M tile, four N tiles) and, when there are fewer blocks
 // than warps, a share of the 8-row k steps of every chunk.  The groups of warps that split
 // the k steps are summed in a fixed order.
@@ -216,12 +217,15 @@ __global__ void __launch_bounds__(256) gram_tc_kernel(int64_t n, Cols<float> A, 
   for (int b = 0; b < BPW; ++b) {
     blk[b] = nblocks < 8 ? (wid % nblocks) : wid + 8 * b;
     const bool ok = active && blk[b] < nblocks && (nblocks < 8 ? b == 0 : true);
-    const int mi = ok ? blk[b] / nbk : 0, nj = ok ? blk[b] % nbk : 0;
-    offA[b][0] = ok ? col_offset(A, mi * 16 + gid, R, lds) : -1;
-    offA[b][1] = ok ? col_offset(A, mi * 16 + gid + 8, R, lds) : -1;
+    int mi = ok ? blk[b] / nbk : 0, nj = ok ? blk[b] % nbk : 0;
+    // upper: a block wholly below the diagonal is not needed
+    const bool need = !(upper && mi * 16 > nj * 32 + 31);
+    mi = need ? mi : 0, nj = need ? nj : 0;
+    offA[b][0] = ok && need ? col_offset(A, mi * 16 + gid, R, lds) : -1;
+    offA[b][1] = ok && need ? col_offset(A, mi * 16 + gid + 8, R, lds) : -1;
 #pragma unroll
-    for (int t = 0; t < 4; ++t) offB[b][t] = ok ? col_offset(B, nj * 32 + t * 8 + gid, R, lds) : -1;
-    if (!ok) blk[b] = -1;
+    for (int t = 0; t < 4; ++t) offB[b][t] = ok && need ? col_offset(B, nj * 32 + t * 8 + gid, R, lds) : -1;
+    if (!ok || !need) blk[b] = -1;
   }
   float acc[BPW][4][4];
 #pragma unroll
@@ -272,9 +276,15 @@ __global__ void __launch_bounds__(256) gram_tc_kernel(int64_t n, Cols<float> A, 
             unsigned bh[2], bl[2];
             split_tf32(offB[b][t] >= 0 ? sb[offB[b][t] + r0 * lds] : 0.f, bh[0], bl[0]);
             split_tf32(offB[b][t] >= 0 ? sb[offB[b][t] + r1 * lds] : 0.f, bh[1], bl[1]);
-            mma_tf32(acc[b][t], ah, bh);
-            mma_tf32(acc[b][t], ah, bl);
-            mma_tf32(acc[b][t], al, bh);
+            // the step's three products from a zero accumulator, then one round-to-nearest
+            // FP32 add per element: the tensor core's own accumulation is not carried across
+            // the hundreds of steps of a CTA (its rounding would bias the running sum)
+            float d[4] = {0.f, 0.f, 0.f, 0.f};
+            mma_tf32(d, al, bh);
+            mma_tf32(d, ah, bl);
+            mma_tf32(d, ah, bh);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[b][t][e] += d[e];
           }
         }
       }
