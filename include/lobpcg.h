@@ -102,6 +102,10 @@ typedef struct {
                                  0 (default) = when the largest stops improving: no 10% drop
                                  in 2 iterations once it is below 1% of its first value, or
                                  in 5 iterations at any level */
+  int autotune;               /* non-zero (default): on the first solve with a given block width,
+                                 time the CSR product kernel families on this matrix (a few
+                                 products per precision, inside that solve) and keep the
+                                 fastest; 0: the built-in choice */
 } lobpcg_options;
 
 typedef struct {
@@ -127,6 +131,9 @@ typedef struct {
                                    (X = V u, W -= Y C, W <- W L^-T, ...), CUDA events per launch */
   double update_fp64_flops;     /* their algorithmic flops, 2 n s q per product */
   int64_t update_fp64_launches; /* their number */
+  int spmm_variant_fp32;        /* CSR product kernel in use: 0 default, 1 row-parallel,
+                                   2 vector gather, 3 band window with global gathers */
+  int spmm_variant_fp64;
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */

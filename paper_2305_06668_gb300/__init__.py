@@ -41,7 +41,7 @@ class _Options(C.Structure):
     _fields_ = [("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
                 ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
-                ("mixed_switch", C.c_double)]
+                ("mixed_switch", C.c_double), ("autotune", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -52,7 +52,8 @@ class _Info(C.Structure):
                 ("spmm_launches", C.c_int64), ("precond_fallback", C.c_int),
                 ("phase_seconds_fp64", C.c_double * 6), ("spmm_launches_fp64", C.c_int64),
                 ("spmm_columns_fp64", C.c_int64), ("update_fp64_seconds", C.c_double),
-                ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64)]
+                ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64),
+                ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int)]
 
 
 def library_path() -> pathlib.Path:
@@ -138,7 +139,8 @@ class Solver:
     def __init__(self, *, diag, row_ptr=None, col_idx=None, val=None, dense=None, extra: int = 0,
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
-                 mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, stream=None):
+                 mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = True,
+                 stream=None):
         torch = _torch()
         L = lib()
         self._keep = [diag, row_ptr, col_idx, val, dense]
@@ -163,6 +165,7 @@ class Solver:
         o.tau_ortho, o.ortho_cap, o.ortho2_cap, o.seed = tau_ortho, ortho_cap, ortho2_cap, seed
         o.profile = 1 if profile else 0
         o.mixed_switch = mixed_switch
+        o.autotune = 1 if autotune else 0
         w = None
         if mlp_weights is not None:
             w = np.ascontiguousarray(mlp_weights, dtype=np.float32)

@@ -88,10 +88,14 @@ __device__ __forceinline__ T warp_max(T v) {
 // most non-zeros (from profile_band); the product then stages that window of X in
 // shared memory.  pure: every entry satisfies |col - row| <= band (the band part of a
 // split matrix), so no gather leaves the window.
+// variant: kSpmmAuto picks by precision, alignment and band; the others force one kernel
+// family (when the blocks allow it): the row-parallel kernel, the vector-gather kernel
+// (no band window), or the band window kernel with global gathers outside the band.
+enum { kSpmmAuto = 0, kSpmmRows = 1, kSpmmVec = 2, kSpmmBand = 3 };
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val,
                      int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band = -1,
-                     bool pure = false);
+                     bool pure = false, int variant = kSpmmAuto);
 // Y += A X for a CSR matrix whose rows hold few, scattered entries (the long-range part of
 // a band / long-range split).  Row-major 16-byte aligned blocks, p <= 32.
 template <class T, class V>

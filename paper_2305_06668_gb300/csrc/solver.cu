@@ -221,8 +221,9 @@ struct SplitCSR {
     band = b;
   }
   // Y = A_band X, then Y += A_lr X
-  void apply(int64_t n, int p, const float* X, int ldx, float* Y, int ldy, cudaStream_t st) const {
-    launch_spmm_csr<float, float>(n, rp_band, ci_band, v_band, p, X, ldx, Y, ldy, st, band, true);
+  void apply(int64_t n, int p, const float* X, int ldx, float* Y, int ldy, cudaStream_t st,
+             int variant = kSpmmAuto) const {
+    launch_spmm_csr<float, float>(n, rp_band, ci_band, v_band, p, X, ldx, Y, ldy, st, band, true, variant);
     if (nnz_lr > 0) launch_spmm_csr_add<float, float>(n, rp_lr, ci_lr, v_lr, p, X, ldx, Y, ldy, st);
   }
   void release() {
@@ -246,6 +247,10 @@ struct lobpcg_ctx {
   // band, product from a shared-memory window of X) and the long-range rest
   SplitCSR sp;
   bool split = false;
+  // CSR product kernels picked by the autotuner for each precision, and the block width
+  // they were timed at (0: not yet)
+  int var32 = kSpmmAuto, var64 = kSpmmAuto;
+  int tuned32 = 0, tuned64 = 0;
   Blocks<double> b64;
   Blocks<float> b32;
   DevBuf small;  // all small FP64 matrices and partials
@@ -328,16 +333,61 @@ int update(lobpcg_ctx& c, const UpdateJob<T>& job, const double* U, int s, int q
   return parts;
 }
 
+// Y = A X with the product kernel chosen for this precision (no statistics).
+template <class T>
+void spmm_product(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
+  const int var = sizeof(T) == 4 ? c.var32 : c.var64;
+  if (c.A.fmt == LOBPCG_CSR && std::is_same<T, float>::value && c.split)
+    c.sp.apply(c.A.n, p, reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy, c.st, var);
+  else if (c.A.fmt == LOBPCG_CSR)
+    launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st, c.band,
+                          false, var);
+  else
+    launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
+}
+
+// Autotuner of the CSR product: on the first solve with block width p, time every kernel
+// family that applies to this matrix and precision (CUDA events, one warm-up and two timed
+// products each, on scratch blocks) and keep the fastest.  The default choice wins ties
+// within 2%.  Candidates: the default (window kernel on the band part of a split FP32
+// matrix, row-parallel for FP64, band window or vector gather otherwise), the row-parallel
+// kernel, the vector-gather kernel and the band window kernel with global gathers.
+template <class T>
+void autotune_spmm(lobpcg_ctx& c, int p, T* X, int ld, T* Y) {
+  int& var = sizeof(T) == 4 ? c.var32 : c.var64;
+  int& tuned = sizeof(T) == 4 ? c.tuned32 : c.tuned64;
+  if (c.A.fmt != LOBPCG_CSR || !c.opt.autotune || p <= 0 || tuned == p) return;
+  std::vector<int> cand = {kSpmmAuto, kSpmmRows, kSpmmVec};
+  if (c.band >= 0) cand.push_back(kSpmmBand);
+  if (sizeof(T) == 4 && c.split) cand = {kSpmmAuto, kSpmmRows, kSpmmBand};  // band part of the split
+  cudaEvent_t e0, e1;
+  LB_CUDA(cudaEventCreate(&e0));
+  LB_CUDA(cudaEventCreate(&e1));
+  int best = kSpmmAuto;
+  float tbest = 0.f;
+  for (int v : cand) {
+    var = v;
+    spmm_product<T>(c, X, ld, p, Y, ld);
+    LB_CUDA(cudaEventRecord(e0, c.st));
+    spmm_product<T>(c, X, ld, p, Y, ld);
+    spmm_product<T>(c, X, ld, p, Y, ld);
+    LB_CUDA(cudaEventRecord(e1, c.st));
+    LB_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    LB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (v == kSpmmAuto || ms < 0.98f * tbest) best = v, tbest = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  var = best;
+  tuned = p;
+}
+
 template <class T>
 void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
   if (p <= 0) return;
   c.prof.mark(PH_SPMM);
-  if (c.A.fmt == LOBPCG_CSR && std::is_same<T, float>::value && c.split)
-    c.sp.apply(c.A.n, p, reinterpret_cast<const float*>(X), ldx, reinterpret_cast<float*>(Y), ldy, c.st);
-  else if (c.A.fmt == LOBPCG_CSR)
-    launch_spmm_csr<T, T>(c.A.n, c.A.row_ptr, c.A.col_idx, Prec<T>::val(c), p, X, ldx, Y, ldy, c.st, c.band);
-  else
-    launch_spmm_dense<T>(c.A.n, Prec<T>::dense(c), Prec<T>::lda(c), p, X, ldx, Y, ldy, c.st);
+  spmm_product<T>(c, X, ldx, p, Y, ldy);
   c.stats.spmm_columns += p;
   c.stats.spmm_launches += 1;
   if (sizeof(T) == 8) c.stats.spmm_launches64 += 1, c.stats.spmm_columns64 += p;
@@ -715,6 +765,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->ortho2_cap = 4;
   opt->seed = 0;
   opt->mlp_weights = nullptr;
+  opt->autotune = 1;
   return LOBPCG_OK;
 }
 
@@ -841,8 +892,10 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     int iters = 0, fp64_iters = 0;
     PhaseOut ph;
     const double tau = c->opt.tau_ortho;
+    autotune_spmm<double>(*c, m, c->b64.W, c->b64.ld, c->b64.AW);
     if (c->opt.precision == LOBPCG_MIXED) {
       c->b32.ensure(n, m);
+      autotune_spmm<float>(*c, m, c->b32.W, c->b32.ld, c->b32.AW);
       launch_colmajor_to_rows<double, float>(n, m, x0, c->b32.X[0], c->b32.ld, c->st);
       const double tau32 = std::max(tau, 3e-5);
       PhaseOut p32 = run_lobpcg<float>(*c, k, m, tol, tau32, c->opt.maxiter, true, c->opt.mixed_switch);
@@ -930,6 +983,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->update_fp64_seconds = c->prof.on ? c->prof.kseconds() : 0.0;
       info->update_fp64_flops = c->prof.on ? c->prof.kflops : 0.0;
       info->update_fp64_launches = c->prof.on ? (int64_t)(c->prof.kused / 2) : 0;
+      info->spmm_variant_fp32 = c->var32;
+      info->spmm_variant_fp64 = c->var64;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))

@@ -937,14 +937,21 @@ __global__ void __launch_bounds__(256) spmm_dense_kernel(int64_t n, const T* __r
 
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p,
-                     const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band, bool pure) {
+                     const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band, bool pure, int variant) {
   if (n <= 0 || p <= 0) return;
   if (p > 32) throw std::invalid_argument("spmm: p > 32");
   constexpr int VEC = 16 / sizeof(T);
   const bool vec_ok = (ldx % VEC == 0) && (ldy % VEC == 0) && ldx >= round_up(p, VEC) &&
                       !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15);
+  // a kernel chosen by the caller (the solver's autotuner); kSpmmAuto: the default choice
+  if (vec_ok && variant == kSpmmRows) {
+    csr_rows_dispatch<T, V, false>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
+    return;
+  }
+  if (variant == kSpmmBand) pure = false;
+  if (variant == kSpmmVec) band = -1;
   if constexpr (std::is_same<T, double>::value) {
-    if (vec_ok) {
+    if (vec_ok && variant == kSpmmAuto) {
       // FP64 is bound by the FMA rate: the row-parallel kernel keeps every lane busy
       csr_rows_dispatch<T, V, false>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
       return;
@@ -1004,9 +1011,9 @@ void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, in
 }
 
 template void launch_spmm_csr<double, double>(int64_t, const int64_t*, const int32_t*, const double*,
-                                              int, const double*, int, double*, int, cudaStream_t, int, bool);
+                                              int, const double*, int, double*, int, cudaStream_t, int, bool, int);
 template void launch_spmm_csr<float, float>(int64_t, const int64_t*, const int32_t*, const float*,
-                                            int, const float*, int, float*, int, cudaStream_t, int, bool);
+                                            int, const float*, int, float*, int, cudaStream_t, int, bool, int);
 
 template <class T, class V>
 void launch_spmm_csr_add(int64_t n, const int64_t* rp, const int32_t* ci, const V* val, int p, const T* X, int ldx,

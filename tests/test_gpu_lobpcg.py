@@ -155,3 +155,27 @@ def test_mixed_precision_reaches_fp64_accuracy(dense):
     _parity(res, ref)
     assert np.max(res.resnorms) <= 1e-8
     assert res.info["fp64_iterations"] < res.info["iterations"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_autotuned_products_give_the_same_eigenpairs(precision):
+    """The product kernel the autotuner picks changes rounding only: eigenpairs agree with
+    the built-in choice (and with the oracle) on a CI-like banded matrix."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=40_009, seed=9)
+    k = 6
+    x0 = synth.diag_guess(a.diag, k + 2, seed=9, noise=0.0)
+    t = lb.upload_csr(a)
+    prec = lb.MIXED if precision == "mixed" else lb.FP64
+    out = {}
+    for tune in (True, False):
+        s = lb.Solver(**t, extra=2, precision=prec, autotune=tune)
+        out[tune] = s.solve(k, 1e-8, X0=torch.from_numpy(x0).cuda())
+        s.close()
+    r1, r0 = out[True], out[False]
+    assert r1.status == 0 and r0.status == 0
+    assert r0.info["spmm_variant_fp64"] == 0 and r0.info["spmm_variant_fp32"] == 0
+    assert 0 <= r1.info["spmm_variant_fp64"] <= 3 and 0 <= r1.info["spmm_variant_fp32"] <= 3
+    assert np.max(rel_eig_err(r1.evals, r0.evals)) <= 1e-10
+    assert np.max(r1.resnorms) <= 1e-8
