@@ -102,10 +102,11 @@ typedef struct {
                                  0 (default) = when the largest stops improving: no 10% drop
                                  in 2 iterations once it is below 1% of its first value, or
                                  in 5 iterations at any level */
-  int autotune;               /* non-zero (default): on the first solve with a given block width,
-                                 time the CSR product kernel families on this matrix (a few
-                                 products per precision, inside that solve) and keep the
-                                 fastest; 0: the built-in choice */
+  int autotune;               /* non-zero: on the first solve with a given block width, time the
+                                 CSR product kernel families on this matrix (a few products per
+                                 precision, inside that solve) and keep the fastest.  Meant for
+                                 contexts reused over many solves (serving, batches).  0
+                                 (default): the built-in choice */
 } lobpcg_options;
 
 typedef struct {

@@ -139,7 +139,7 @@ class Solver:
     def __init__(self, *, diag, row_ptr=None, col_idx=None, val=None, dense=None, extra: int = 0,
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
-                 mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = True,
+                 mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
                  stream=None):
         torch = _torch()
         L = lib()

@@ -765,7 +765,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->ortho2_cap = 4;
   opt->seed = 0;
   opt->mlp_weights = nullptr;
-  opt->autotune = 1;
+  opt->autotune = 0;
   return LOBPCG_OK;
 }
 
