@@ -253,7 +253,8 @@ def test_spmm_csr_f32_split_empty_rows_and_heavy_rows():
 
 
 @pytest.mark.parametrize("n,p,q,ld", [(1, 1, 1, 4), (97, 5, 3, 8), (10_007, 21, 21, 24), (100_003, 63, 63, 64),
-                                      (50_001, 42, 21, 44), (4_099, 96, 40, 96), (20_011, 16, 16, 17)])
+                                      (50_001, 42, 21, 44), (4_099, 96, 40, 96), (7_001, 96, 96, 96),
+                                      (20_011, 16, 16, 17)])
 def test_gram_f32_matches_oracle(n, p, q, ld):
     """FP32 Gram (tensor-core 3xTF32 path when ld is a multiple of 4, FP32 FMA otherwise)
     against the FP64 oracle on the FP32-rounded blocks: |C - ref| <= 2^-19 |X|^T |Y| + a
