@@ -28,6 +28,9 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
     o = lb._Options()
     assert L.lobpcg_options_default(ctypes.byref(o)) == lb.OK
     assert o.maxiter == 1000 and o.tau_ortho == 1e-14 and o.precond == lb.PREC_DIAG
+    assert o.precision == lb.FP64 and o.ortho_cap == 6 and o.ortho2_cap == 4 and o.extra == 0
+    assert o.autotune == 0 and o.mixed_switch == 0.0 and o.profile == 0
+    assert ctypes.sizeof(lb._Info) >= 8 * 6 * 2  # the info struct the binding reads
     assert L.lobpcg_options_default(None) == lb.EINVAL
     # NULL arguments are rejected before any device work
     ctx = ctypes.c_void_p()
@@ -35,6 +38,12 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
     assert b"NULL" in L.lobpcg_last_error(None)
     assert L.lobpcg_solve(None, 1, ctypes.c_double(1e-8), None, None, None, None, None) == lb.EINVAL
     L.lobpcg_destroy(None)  # NULL-safe
+    # building blocks reject bad sizes on the host, before any device work
+    assert L.lobpcg_syev2_f64(ctypes.c_int(0), None, ctypes.c_double(0.0), None, None, None) == lb.EINVAL
+    assert L.lobpcg_gram_f32(ctypes.c_int64(10), ctypes.c_int(97), None, ctypes.c_int(97), ctypes.c_int(1), None,
+                             ctypes.c_int(1), None, None) == lb.EINVAL
+    assert L.lobpcg_spmm_csr_f32(ctypes.c_int64(10), None, None, None, ctypes.c_int64(0), ctypes.c_int(1), None,
+                                 ctypes.c_int(4), None, ctypes.c_int(4), ctypes.c_int(-1), None, None) == lb.EINVAL
 
 
 def test_no_cpu_fallback_in_product_package():
