@@ -46,6 +46,10 @@ namespace {
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }  // also on an exception between allocation and the explicit release
   void ensure(size_t b) {
     if (b <= bytes) return;
     if (p) cudaFree(p);
