@@ -239,12 +239,12 @@ LOBPCG_API lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, do
 
 /* Same contract, two-stage method (the Rayleigh-Ritz solve of the FP32 phase of the mixed
  * form): FP32 Jacobi, one FP64 Cholesky-QR of its rotation matrix Q, then Jacobi on
- * Q^T a Q accumulated into Q until its off-diagonal mass is <= tol ||a||_F.  tol = 0 means
- * 1e-15: FP64 rotations, eigenvalues and residuals to FP64 absolute accuracy (~eps ||a||),
- * U orthonormal to FP64 rounding.  1e-12 <= tol < 1e-6 (the solver uses 1e-10): the
- * rotations of that last stage update the small off-diagonal part in FP32 (diagonal and
- * rotation product in FP64), good to about tol.  Exact zero
- * couplings of a are not kept.  EINVAL for tol outside [0, 1e-6). */
+ * Q^T a Q accumulated into Q until its off-diagonal mass is <= tol ||a||_F (tol = 0 means
+ * 1e-15).  tol < 1e-12: FP64 rotations; eigenvalues and residuals to FP64 absolute accuracy
+ * (~eps ||a||), U orthonormal to FP64 rounding.  1e-12 <= tol < 1e-6 (the solver uses
+ * 1e-10): the rotations of that last stage update the small off-diagonal part in FP32
+ * (diagonal and rotation product in FP64), good to about tol.  Exact zero couplings of a
+ * are not kept.  EINVAL for tol outside [0, 1e-6). */
 LOBPCG_API lobpcg_status lobpcg_syev2_f64(int s, const double* a, double tol, double* lam, double* U,
                                           lobpcg_stream stream);
 
