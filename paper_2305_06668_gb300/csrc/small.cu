@@ -74,7 +74,7 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // phase A: rotation of every pair of this round (circle method, player N-1 fixed)
+      // phase A: rotation of every pair of this Jacobi round (circle method, player N-1 fixed)
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
         if (i == 0) p = N - 1, q = r;
