@@ -278,6 +278,7 @@ int oracle_jacobi_eig(int s, const double* a_in, double* lam, double* U) {
 /* SVQB step (Stathopoulos & Wu), the fallback when even shifted Cholesky fails:
  * D = diag(M)^{-1/2}, D M D = Z Theta Z^T, X <- X D Z Theta^{-1/2}. */
 void oracle_svqb(int64_t n, int p, double* X, const double* M) {
+  if (p <= 0) return;
   double* dmd = (double*)malloc(sizeof(double) * (size_t)p * p);
   double* Z = (double*)malloc(sizeof(double) * (size_t)p * p);
   double* th = (double*)malloc(sizeof(double) * (size_t)p);
