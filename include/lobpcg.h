@@ -222,6 +222,21 @@ LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64
 LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int ldx, int q, const double* Y,
                               int ldy, double* C, lobpcg_stream stream);
 
+/* The block update of Algorithm 1 for FP32 blocks: X = base + alpha [V_0 .. V_{nseg-1}] U
+ * and, with AV, AX = alpha [AV_0 ..] U (the basis and residual update X <- V u_x, AX <- AV u_x,
+ * and P <- V u_p).  V_g, AV_g: device, n x w[g] row-major with row stride ld floats
+ * (1 <= nseg <= 3, s = sum of w[g] <= 96, w[g] <= ld).  U: device FP64, s x q column-major,
+ * q <= 32.  base (nullable, X only) and X, AX: device, row-major, strides ld_base, ld_out
+ * >= q; X may alias base or V_0 (in place).  With resnorm (host, q doubles; needs AV, lam
+ * and no base): resnorm[j] = || AX_j - lam_j X_j ||_2, lam device FP64 (q).  Products are
+ * FP32 FMAs in the order of the rows of U.  Rows 16-byte aligned with ld a multiple of 4
+ * take the staged kernel; other layouts a general one with the same arithmetic.
+ * EINVAL for bad sizes or NULL pointers. */
+LOBPCG_API lobpcg_status lobpcg_update_f32(int64_t n, int nseg, const float* const* V, const float* const* AV,
+                                          const int* w, int ld, const double* U, int q, double alpha,
+                                          const float* base, int ld_base, float* X, float* AX, int ld_out,
+                                          const double* lam, double* resnorm, lobpcg_stream stream);
+
 /* C = X^T Y for FP32 blocks, the Gram of the mixed form (Algorithm 1's projected matrices
  * with FP32 storage).  X: n x p float (ldx), Y: n x q float (ldy), p, q <= 96.  C: device,
  * FP64, column-major p x q.  When the rows are 16-byte aligned with ldx == ldy a multiple

@@ -72,7 +72,7 @@ def lib():
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
-                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32"):
+                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -273,6 +273,42 @@ def gram_f32(X, Y, stream=None):
     _check(lib().lobpcg_gram_f32(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
                                  C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
     return Cm.t()
+
+
+def update_f32(V, U, q=None, alpha=1.0, AV=None, base=None, X=None, AX=None, lam=None, resnorm=False,
+               stream=None):
+    """X = base + alpha [V_0 ..] U and, with AV, AX = alpha [AV_0 ..] U (FP32 block update).
+
+    V (and AV): a list of 1 to 3 float32 CUDA tensors (n x w_g views sharing one row
+    stride); U: float64 CUDA (s x q) with s = sum of w_g.  base, X, AX: optional float32
+    (n x q, X and AX sharing one row stride; X may be base or V[0] for an in-place update).
+    With resnorm=True (AV and lam given, no base) also returns || AX_j - lam_j X_j ||_2.
+    Returns X, or (X, AX), or (X, AX, resnorm).
+    """
+    torch = _torch()
+    V = list(V)
+    n = V[0].shape[0]
+    ws = [int(v.shape[1]) for v in V]
+    ld = int(V[0].stride(0))
+    q = int(U.shape[1]) if q is None else int(q)
+    if X is None:
+        X = torch.empty((n, q), dtype=torch.float32, device=V[0].device)
+    if AV is not None and AX is None:
+        AX = torch.empty_like(X)
+    Ucol = U if (U.stride(0) == 1 and U.stride(1) == U.shape[0]) else U.t().contiguous().t()  # column-major
+    vp = (C.c_void_p * len(V))(*[v.data_ptr() for v in V])
+    ap = (C.c_void_p * len(V))(*[a.data_ptr() for a in AV]) if AV is not None else None
+    warr = (C.c_int * len(V))(*ws)
+    rn = (C.c_double * q)() if resnorm else None
+    _check(lib().lobpcg_update_f32(C.c_int64(n), C.c_int(len(V)), vp, ap, warr, C.c_int(ld), _ptr(Ucol),
+                                   C.c_int(q), C.c_double(alpha), _ptr(base),
+                                   C.c_int(base.stride(0) if base is not None else 0), _ptr(X), _ptr(AX),
+                                   C.c_int(X.stride(0)), _ptr(lam), rn, _stream(stream)))
+    if AV is None:
+        return X
+    if resnorm:
+        return X, AX, np.array(rn[:])
+    return X, AX
 
 
 def gram_noalloc(X, Y, out=None, stream=None):

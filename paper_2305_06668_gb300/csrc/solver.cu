@@ -1127,6 +1127,47 @@ extern "C" lobpcg_status lobpcg_gram_f32(int64_t n, int p, const float* X, int l
   });
 }
 
+extern "C" lobpcg_status lobpcg_update_f32(int64_t n, int nseg, const float* const* V, const float* const* AV,
+                                           const int* w, int ld, const double* U, int q, double alpha,
+                                           const float* base, int ld_base, float* X, float* AX, int ld_out,
+                                           const double* lam, double* resnorm, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && nseg >= 1 && nseg <= 3 && V && w && U && X,
+            "lobpcg_update_f32: NULL argument, n < 1 or nseg outside 1..3");
+    require(!AV == !AX, "lobpcg_update_f32: AV and AX go together");
+    require(!resnorm || (AV && lam && !base), "lobpcg_update_f32: resnorm needs AV, AX, lam and no base");
+    int s = 0;
+    Cols<float> cv{}, ca{};
+    for (int g = 0; g < nseg; ++g) {
+      require(V[g] && (!AV || AV[g]) && w[g] >= 0 && w[g] <= ld, "lobpcg_update_f32: NULL segment or w > ld");
+      cv = cols_add<float>(cv, V[g], ld, w[g]);
+      if (AV) ca = cols_add<float>(ca, AV[g], ld, w[g]);
+      s += w[g];
+    }
+    require(s >= 1 && s <= kMaxS && q >= 1 && q <= 32 && ld_out >= q && (!base || ld_base >= q),
+            "lobpcg_update_f32: need 1 <= s <= 96, 1 <= q <= 32, ld_out >= q, ld_base >= q");
+    ScratchCtx sc(n, reinterpret_cast<cudaStream_t>(stream));
+    UpdateJob<float> job{};
+    job.in[0] = cv, job.in[1] = ca;
+    job.out[0] = X, job.out[1] = AX;
+    job.ld_out[0] = job.ld_out[1] = ld_out;
+    job.base[0] = base;
+    job.ld_base[0] = ld_base;
+    job.nprod = AV ? 2 : 1;
+    const int parts = update<float>(sc.c, job, U, s, q, alpha, resnorm ? lam : nullptr,
+                                    resnorm ? sc.c.npart : nullptr);
+    if (resnorm) {
+      // per-column sums of the partial squared norms (entries 0..q-1 of each part's 2q)
+      reduce_partials(sc.c.npart, parts, 2 * q, sc.c.G, sc.c.st);
+      LB_CUDA(cudaMemcpyAsync(sc.c.host, sc.c.G, (size_t)q * sizeof(double), cudaMemcpyDeviceToHost, sc.c.st));
+    }
+    sc.c.sync();
+    if (resnorm)
+      for (int j = 0; j < q; ++j) resnorm[j] = std::sqrt(sc.c.host[j]);
+    return LOBPCG_OK;
+  });
+}
+
 extern "C" lobpcg_status lobpcg_syev_f64(int s, const double* a, double* lam, double* U,
                                          lobpcg_stream stream) {
   return guarded(nullptr, [&]() -> lobpcg_status {

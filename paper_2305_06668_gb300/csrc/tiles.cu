@@ -478,7 +478,8 @@ __global__ void __launch_bounds__(256) update_pipe_kernel(int64_t n, UpdateJob<T
 // ------------------------------------------------------------------------ update, one row per thread
 // out_t = base_t + alpha * in_t * U with U (s x q, q <= QMAX) broadcast from shared memory
 // and each thread streaming its own input row with 16-byte loads (the row's lines stay
-// in L1 while the thread walks them).  Used for every update of the solver.
+// in L1 while the thread walks them).  The FP32 fallback of update_stage_kernel (products
+// whose segments differ in width, or the norm form with a base).
 template <class T>
 struct V16;
 template <>
@@ -607,6 +608,262 @@ int update_row_launch(int64_t n, const UpdateJob<T>& job, int ld, const double* 
   return (int)ctas;
 }
 
+// ------------------------------------------------------------------------ update, staged slabs
+// out_t = base_t + alpha * in_t * U for FP32 blocks, q <= QMAX: the arithmetic of
+// update_row_kernel (same rows per thread, the same FMA chain in the order of the rows of
+// U), with the memory traffic and the instruction stream reorganised.
+//  - The CTA's rows pass through shared memory in slabs of kStageRows rows x one input
+//    segment of one product: cp.async copies the slabs kStageSlabs - 1 ahead of use
+//    (coalesced 16-byte reads, in flight while the FMAs run).  Columns past the segment's
+//    width are zero-filled, and U's rows sit in shared memory with each segment padded to a
+//    multiple of 4 zero rows, so the inner loop runs over whole 16-byte vectors of x with no
+//    bounds test (the padding adds exact zeros to the sums).
+//  - Thread r multiplies row r of each slab by U (16-byte broadcasts), writes its results
+//    over its own row of the product's last slab, and the CTA stores the slab's rows with
+//    16-byte stores, 4 rows per warp pass.
+// With NORM (nprod == 2, no base) the per-column partial sums of r_ij^2 and max |r_ij|,
+// r = AX - X diag(lam), go to norm_part[cta][2q].
+constexpr int kStageRows = 256, kStageSlabs = 3;
+
+template <class T>
+__device__ __forceinline__ const T* seg_ptr(const Cols<T>& c, int g) {
+  return g == 0 ? c.p[0] : (g == 1 ? c.p[1] : c.p[2]);
+}
+template <class T>
+__device__ __forceinline__ int seg_w(const Cols<T>& c, int g) {
+  return g == 0 ? c.w[0] : (g == 1 ? c.w[1] : c.w[2]);
+}
+__host__ __device__ __forceinline__ int padded_rows(int w) { return (w + 3) / 4 * 4; }
+
+template <int QMAX, bool NORM>
+__global__ void __launch_bounds__(kStageRows, 2) update_stage_kernel(int64_t n, UpdateJob<float> job, int ld,
+                                                                     int lds, const double* __restrict__ U, int s,
+                                                                     int q, double alpha,
+                                                                     const double* __restrict__ lam,
+                                                                     double* __restrict__ norm_part,
+                                                                     int64_t rows_per_cta) {
+  constexpr int QV = QMAX / 4;  // float4 vectors per U row
+  constexpr int R = kStageRows, S = kStageSlabs;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nseg = job.in[0].nseg;
+  int sp = 0;  // padded rows of U
+  for (int g = 0; g < nseg; ++g) sp += padded_rows(seg_w(job.in[0], g));
+  float4* sU = reinterpret_cast<float4*>(smem_raw);  // sp rows of QV vectors
+  float* ring = reinterpret_cast<float*>(sU + sp * QV);  // S slabs of R rows, row stride lds
+  {
+    float* su = reinterpret_cast<float*>(sU);
+    int l0 = 0, p0 = 0;
+    for (int g = 0; g < nseg; ++g) {
+      const int w = seg_w(job.in[0], g), wp = padded_rows(w);
+      for (int e = threadIdx.x; e < wp * QMAX; e += blockDim.x) {
+        const int l = e / QMAX, j = e % QMAX;
+        su[(p0 + l) * QMAX + j] = (l < w && j < q) ? (float)U[l0 + l + j * s] : 0.f;
+      }
+      l0 += w, p0 += wp;
+    }
+  }
+  const int per_chunk = job.nprod * nseg;
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  const int nchunks = (int)((r_end - r_begin + R - 1) / R);
+  const int total = nchunks * per_chunk;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // copy slab v (rows of chunk v / per_chunk; product, segment from v % per_chunk) to its
+  // slot: a warp copies 32 / nv whole rows per pass, lane (rr, c) the c-th 16 bytes of row
+  // rr, zero-filling the columns past w and the rows past the end
+  auto issue = [&](int v) {
+    const int k = v / per_chunk, u = v - k * per_chunk;
+    const int t = u / nseg, g = u - t * nseg;
+    const Cols<float>& in = t == 0 ? job.in[0] : job.in[1];
+    const float* src = seg_ptr(in, g);
+    const int w = seg_w(in, g);
+    const int nv = (w + 3) / 4;  // 1..24 (w <= 96)
+    if (nv == 0) return;
+    const int rpi = 32 / nv, rr = lane / nv, c = lane - rr * nv;
+    if (rr >= rpi) return;
+    const int bytes = min(4, w - 4 * c) * 4;
+    float* dst = ring + (v % S) * R * lds + c * 4;
+    const int64_t r0 = r_begin + (int64_t)k * R;
+    for (int r = wid * rpi + rr; r < R; r += nw * rpi) {
+      const int64_t row = r0 + r;
+      const bool ok = row < r_end;
+      const unsigned sa = (unsigned)__cvta_generic_to_shared(dst + r * lds);
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(sa),
+                   "l"(src + (ok ? row : 0) * ld + c * 4), "r"(ok ? bytes : 0));
+    }
+  };
+  float nsum[NORM ? QMAX : 1], nmax[NORM ? QMAX : 1];  // per-thread partial column sums of r^2, max |r|
+  if (NORM)
+#pragma unroll
+    for (int j = 0; j < QMAX; ++j) nsum[j] = 0.f, nmax[j] = 0.f;
+#pragma unroll
+  for (int v = 0; v < S - 1; ++v) {
+    if (v < total) issue(v);
+    cp_async_commit();
+  }
+  const int qv = (q + 3) / 4;
+  const int fr = lane >> 3, fc = (lane & 7) * 4;  // write-back: row fr of 4, columns fc..fc+3
+  int v = 0;
+  for (int k = 0; k < nchunks; ++k) {
+    const int64_t r0 = r_begin + (int64_t)k * R;
+    const bool live = r0 + threadIdx.x < r_end;
+    float x_res[NORM ? QMAX : 1];  // this row's X result, kept for the residual of AX
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= job.nprod) break;
+      const Cols<float>& in = job.in[t];
+      float acc[QMAX];
+#pragma unroll
+      for (int j = 0; j < QMAX; ++j) acc[j] = 0.f;
+      float* slab = ring;
+      const float4* useg = sU;
+      for (int g = 0; g < nseg; ++g, ++v) {
+        cp_async_wait<S - 2>();
+        __syncthreads();
+        if (v + S - 1 < total) issue(v + S - 1);
+        cp_async_commit();
+        slab = ring + (v % S) * R * lds;
+        const float* xr = slab + threadIdx.x * lds;
+        const int nv = (seg_w(in, g) + 3) / 4;
+        for (int c = 0; c < nv; ++c) {
+          const float4 xv = *reinterpret_cast<const float4*>(xr + 4 * c);
+          const float4* ur = useg + 4 * c * QV;
+          const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+#pragma unroll
+            for (int jv = 0; jv < QV; ++jv) {
+              const float4 u = ur[i * QV + jv];
+              acc[jv * 4 + 0] = fmaf(xs[i], u.x, acc[jv * 4 + 0]);
+              acc[jv * 4 + 1] = fmaf(xs[i], u.y, acc[jv * 4 + 1]);
+              acc[jv * 4 + 2] = fmaf(xs[i], u.z, acc[jv * 4 + 2]);
+              acc[jv * 4 + 3] = fmaf(xs[i], u.w, acc[jv * 4 + 3]);
+            }
+          }
+        }
+        useg += 4 * nv * QV;
+      }
+      // this thread's results over its own row of the last slab (only thread r reads row r)
+      float* own = slab + threadIdx.x * lds;
+#pragma unroll
+      for (int jv = 0; jv < QV; ++jv) {
+        if (jv < qv) {
+          float4 o;
+          o.x = (float)alpha * acc[jv * 4 + 0];
+          o.y = (float)alpha * acc[jv * 4 + 1];
+          o.z = (float)alpha * acc[jv * 4 + 2];
+          o.w = (float)alpha * acc[jv * 4 + 3];
+          *reinterpret_cast<float4*>(own + 4 * jv) = o;
+        }
+      }
+      if (NORM) {
+#pragma unroll
+        for (int j = 0; j < QMAX; ++j) {
+          const float val = (float)alpha * acc[j];
+          if (t == 0) {
+            x_res[j] = val;
+          } else if (live && j < q) {
+            const float rij = fmaf(-(float)lam[j], x_res[j], val);  // AX - lam X, one rounding
+            nsum[j] = fmaf(rij, rij, nsum[j]);
+            nmax[j] = fmaxf(nmax[j], fabsf(rij));
+          }
+        }
+      }
+      __syncthreads();
+      // the slab's rows back to out_t (+ base_t): 4 rows x 8 lanes of 4 columns per pass
+      float* out = job.out[t];
+      const float* base = job.base[t];
+      const int ldo = job.ld_out[t], ldb = job.ld_base[t];
+      const bool vec = !(ldo & 3) && !(reinterpret_cast<uintptr_t>(out) & 15) &&
+                       (!base || (!(ldb & 3) && !(reinterpret_cast<uintptr_t>(base) & 15)));
+      if (fc < q) {
+        for (int r = wid * 4 + fr; r < R; r += nw * 4) {
+          const int64_t row = r0 + r;
+          if (row >= r_end) break;
+          const float* sv = slab + r * lds + fc;
+          float* o = out + row * ldo + fc;
+          const float* b = base ? base + row * ldb + fc : nullptr;
+          if (vec && fc + 4 <= q) {
+            float4 val = *reinterpret_cast<const float4*>(sv);
+            if (b) {
+              const float4 bv = *reinterpret_cast<const float4*>(b);
+              val.x = bv.x + val.x, val.y = bv.y + val.y, val.z = bv.z + val.z, val.w = bv.w + val.w;
+            }
+            *reinterpret_cast<float4*>(o) = val;
+          } else {
+#pragma unroll
+            for (int jj = 0; jj < 4; ++jj)
+              if (fc + jj < q) o[jj] = b ? b[jj] + sv[jj] : sv[jj];
+          }
+        }
+      }
+    }
+  }
+  cp_async_wait<0>();
+  if (!NORM) return;
+  // CTA reduction of the per-column partial norms: warp shuffles, then warps in order
+  __syncthreads();
+  double* red = reinterpret_cast<double*>(ring);  // [warps][2 * QMAX]
+#pragma unroll
+  for (int j = 0; j < QMAX; ++j) {
+    if (j >= q) break;
+    const double a = warp_sum((double)nsum[j]);
+    const double m = warp_max((double)nmax[j]);
+    if (lane == 0) red[wid * 2 * QMAX + j] = a, red[wid * 2 * QMAX + QMAX + j] = m;
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += blockDim.x) {
+    double a = 0.0, m = 0.0;
+    for (int w2 = 0; w2 < nw; ++w2) a += red[w2 * 2 * QMAX + j], m = fmax(m, red[w2 * 2 * QMAX + QMAX + j]);
+    norm_part[(int64_t)blockIdx.x * 2 * q + j] = a;
+    norm_part[(int64_t)blockIdx.x * 2 * q + q + j] = m;
+  }
+}
+
+// padded rows of U for the segments of `c`
+inline int stage_u_rows(const Cols<float>& c) {
+  int sp = 0;
+  for (int g = 0; g < c.nseg; ++g) sp += padded_rows(c.w[g]);
+  return sp;
+}
+
+inline size_t stage_smem(const Cols<float>& c, int qmax, int ld) {
+  return (size_t)stage_u_rows(c) * qmax * sizeof(float) +
+         (size_t)kStageSlabs * kStageRows * padded_ld<float>(ld) * sizeof(float);
+}
+
+template <int QMAX, bool NORM>
+int update_stage_launch(int64_t n, const UpdateJob<float>& job, int ld, const double* U, int s, int q, double alpha,
+                        const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  const int lds = padded_ld<float>(ld);
+  const size_t smem = stage_smem(job.in[0], QMAX, ld);
+  // set once per process; function-local statics initialise thread-safely
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(update_stage_kernel<QMAX, NORM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    return true;
+  }();
+  (void)attr;
+  // the rows of each CTA and thread as in update_row_launch
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, kStageRows));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = ceil_div(n, ctas);
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  update_stage_kernel<QMAX, NORM><<<(unsigned)ctas, kStageRows, smem, st>>>(n, job, ld, lds, U, s, q, alpha, lam,
+                                                                           norm_part, rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
+template <bool NORM>
+int update_stage_dispatch(int64_t n, const UpdateJob<float>& job, int ld, const double* U, int s, int q,
+                          double alpha, const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  if (q <= 8) return update_stage_launch<8, NORM>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  if (q <= 16) return update_stage_launch<16, NORM>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  if (q <= 24) return update_stage_launch<24, NORM>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+  return update_stage_launch<32, NORM>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+}
+
 int count_tiles(int pa, int pb, int TI, int TJ, bool upper) {
   const int nti = (pa + TI - 1) / TI, ntj = (pb + TJ - 1) / TJ;
   int ntiles = 0;
@@ -698,6 +955,19 @@ int launch_update_pipe(int64_t n, const UpdateJob<T>& job, const double* U, int 
   const int ld = job.in[0].ld[0];
   for (int t = 0; t < job.nprod; ++t)
     if (!aligned(job.in[t], ld) || job.in[t].nseg != job.in[0].nseg) return 0;
+  // staged slabs (FP32): outputs no wider than a slab row and 32 columns, the products'
+  // segments of equal widths, the norm form as the solver uses it
+  if constexpr (sizeof(T) == 4) {
+    bool same_w = true;
+    for (int t = 1; t < job.nprod; ++t)
+      for (int g = 0; g < job.in[0].nseg; ++g) same_w = same_w && job.in[t].w[g] == job.in[0].w[g];
+    if (same_w && q <= 32 && q <= padded_ld<T>(ld) && s <= kMaxS && stage_smem(job.in[0], 32, ld) <= 200 * 1024) {
+      if (!norm_part)
+        return update_stage_dispatch<false>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+      if (job.nprod == 2 && !job.base[0] && !job.base[1])
+        return update_stage_dispatch<true>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
+    }
+  }
   if (q <= 8) return update_row_launch<T, 8>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
   if (q <= 16) return update_row_launch<T, 16>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);
   if (q <= 24) return update_row_launch<T, 24>(n, job, ld, U, s, q, alpha, lam, norm_part, max_ctas, st);

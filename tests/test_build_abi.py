@@ -44,6 +44,15 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
                              ctypes.c_int(1), None, None) == lb.EINVAL
     assert L.lobpcg_spmm_csr_f32(ctypes.c_int64(10), None, None, None, ctypes.c_int64(0), ctypes.c_int(1), None,
                                  ctypes.c_int(4), None, ctypes.c_int(4), ctypes.c_int(-1), None, None) == lb.EINVAL
+    # update: nseg outside 1..3, then q > 32 with valid-looking (never dereferenced) pointers
+    dummy = (ctypes.c_void_p * 3)(16, 16, 16)
+    w = (ctypes.c_int * 3)(4, 4, 4)
+    upd = lambda nseg, q: L.lobpcg_update_f32(ctypes.c_int64(10), ctypes.c_int(nseg), dummy, None, w, ctypes.c_int(4),
+                                              ctypes.c_void_p(16), ctypes.c_int(q), ctypes.c_double(1.0), None,
+                                              ctypes.c_int(0), ctypes.c_void_p(16), None, ctypes.c_int(q), None, None,
+                                              None)
+    assert upd(4, 4) == lb.EINVAL and upd(0, 4) == lb.EINVAL
+    assert upd(1, 33) == lb.EINVAL and b"q <= 32" in L.lobpcg_last_error(None)
 
 
 def test_no_cpu_fallback_in_product_package():

@@ -273,3 +273,73 @@ def test_gram_f32_matches_oracle(n, p, q, ld):
     rows_per_cta = max(64, n // 304 + 64)
     tol = (2.0 ** -19 + rows_per_cta * np.finfo(np.float32).eps) * scale + 1e-30
     assert np.all(np.abs(Cg - ref) <= tol)
+
+
+@pytest.mark.parametrize("n,ws,ld,q,mode", [
+    (7001, (21, 21, 21), 24, 21, "pair_norm"),      # X, AX = [X W P] u_x with residual norms
+    (200_000, (21, 21, 21), 24, 21, "pair_norm"),   # several 256-row chunks per CTA, ragged end
+    (100_003, (21, 17, 9), 24, 19, "pair"),         # P, AP = V u_p
+    (50_001, (21, 14), 24, 14, "base_inplace"),     # W -= Y C (alpha = -1, W is base and output)
+    (30_011, (21,), 24, 16, "right_inplace"),       # W <- W S, q < w
+    (20_000, (32, 32, 32), 32, 32, "pair_norm"),    # s = 96, q = 32
+    (4_099, (3, 4), 8, 5, "plain"),
+    (1, (2,), 4, 2, "pair_norm"),
+    (9_001, (21, 5), 21, 13, "plain"),              # row stride not a multiple of 4: general kernel
+])
+def test_update_f32_matches_oracle(n, ws, ld, q, mode):
+    """FP32 block update X = base + alpha [V_g] U (and AX, residual norms) against the
+    oracle's FP64 product of the same FP32-rounded V and U: |X - ref| <= (s + 2) 2^-24 |V| |U|
+    per element (FP32 FMA chain over s terms, then the scale and the base add)."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    s = sum(ws)
+    r32 = lambda M: M.astype(np.float32).astype(np.float64)
+    Vs = [r32(synth.gaussian_block(n, w, seed=100 + i)) for i, w in enumerate(ws)]
+    AVs = [r32(synth.gaussian_block(n, w, seed=200 + i)) for i, w in enumerate(ws)]
+    U = synth.gaussian_block(s, q, seed=7) / np.sqrt(s)
+    lam = np.linspace(-1.0, 2.0, q)
+    alpha = -1.0 if mode == "base_inplace" else 1.0
+
+    def block32(M, stride):
+        buf = torch.full((n, stride), float("nan"), dtype=torch.float32, device="cuda")  # padding poisoned
+        buf[:, :M.shape[1]] = torch.from_numpy(M.astype(np.float32)).cuda()
+        return buf[:, :M.shape[1]]
+
+    Vd = [block32(M, ld) for M in Vs]
+    AVd = [block32(M, ld) for M in AVs]
+    Ud = torch.from_numpy(U).cuda()
+    Vcat, AVcat = np.hstack(Vs), np.hstack(AVs)
+    U32 = r32(U)
+    ref = oracle.gram(Vcat.T.copy(), U32)          # (n x s)(s x q) as a Gram over the s rows
+    scale = np.abs(Vcat) @ np.abs(U32)
+    tol = (s + 2) * 2.0 ** -24 * scale + 1e-30
+    if mode in ("pair_norm", "pair"):
+        X, AX, *rest = lb.update_f32(Vd, Ud, AV=AVd, lam=torch.from_numpy(lam).cuda(),
+                                     resnorm=(mode == "pair_norm"))
+        aref = oracle.gram(AVcat.T.copy(), U32)
+        atol = (s + 2) * 2.0 ** -24 * (np.abs(AVcat) @ np.abs(U32)) + 1e-30
+        Xh, AXh = X.cpu().numpy().astype(np.float64), AX.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(Xh - ref) <= tol)
+        assert np.all(np.abs(AXh - aref) <= atol)
+        if rest:
+            # the residual of the FP32 results, formed in FP32 per element and summed in FP64
+            R = AXh - Xh * lam[None, :]
+            rn_ref = np.sqrt(np.sum(R * R, axis=0))
+            rtol = 8 * 2.0 ** -24 * np.sqrt(np.sum((np.abs(AXh) + np.abs(Xh * lam[None, :])) ** 2, axis=0))
+            assert np.all(np.abs(rest[0] - rn_ref) <= rtol + 1e-300)
+    elif mode == "base_inplace":
+        W0 = r32(synth.gaussian_block(n, q, seed=9))
+        W = block32(W0, ld)
+        out = lb.update_f32(Vd, Ud, alpha=alpha, base=W, X=W)
+        assert out.data_ptr() == W.data_ptr()
+        Wh = W.cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(Wh - (W0 - ref)) <= tol + 2.0 ** -24 * np.abs(W0))
+    elif mode == "right_inplace":
+        out = lb.update_f32(Vd, Ud, X=Vd[0][:, :q])
+        Wh = Vd[0][:, :q].cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(Wh - ref) <= tol)
+        # the columns past q are left as they were
+        assert np.array_equal(Vd[0][:, q:].cpu().numpy(), Vs[0][:, q:].astype(np.float32))
+    else:
+        X = lb.update_f32(Vd, Ud)
+        assert np.all(np.abs(X.cpu().numpy().astype(np.float64) - ref) <= tol)
