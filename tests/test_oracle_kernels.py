@@ -72,6 +72,27 @@ def test_gram_matches_matmul(n, p, q):
     assert np.max(np.abs(C - X.T @ Y)) <= 1e-13 * np.sqrt(n) * 4
 
 
+def test_gram_as_block_product_with_many_outputs():
+    """The block product V U (n x s times s x q) written as the Gram (V^T)^T U over s rows,
+    the form the FP32 update parity test uses: checked element by element against integer
+    arithmetic (exact) and against a float product (every entry of the n x q result, with
+    n far above the Gram's usual widths)."""
+    g = np.random.default_rng(5)
+    n, s, q = 20_011, 63, 21
+    # small integers: every product and sum is exact in FP64, so the result must be exact
+    Vi = g.integers(-64, 65, size=(n, s))
+    Ui = g.integers(-64, 65, size=(s, q))
+    C = oracle.gram(Vi.T.astype(np.float64).copy(), Ui.astype(np.float64))
+    assert C.shape == (n, q)
+    assert np.array_equal(C, (Vi @ Ui).astype(np.float64))
+    # general values: within the pairwise-summation bound of the exact product
+    V = g.standard_normal((n, s))
+    U = g.standard_normal((s, q))
+    C = oracle.gram(V.T.copy(), U)
+    scale = np.abs(V) @ np.abs(U)
+    assert np.all(np.abs(C - V @ U) <= 8 * np.finfo(float).eps * scale)
+
+
 def test_apply_matches_scipy_and_dense():
     a = synth.sparse_cfg1(n=600, seed=3)
     X = synth.gaussian_block(600, 5, seed=1)
