@@ -31,8 +31,8 @@ if ROOT not in sys.path:
 METRIC = "time to k eigenpairs at \u2016r\u2016\u22641e-8: mixed+learned vs plain FP64 LOBPCG, 1 GB300"
 N_ROWS, K, EXTRA, TOL, SEED = 2_000_000, 16, 5, 1e-8, 0
 # DRAM bytes (read + write) per FP64 block-update launch, averaged over the 52 update
-# launches of two solves in the ncu capture of profiles/update_fp64_ci1m.md (687 MB at
-# n = 10^6), scaled to n = 2*10^6 by the rows processed
+# launches of two solves in an ncu capture at n = 10^6 (687 MB), scaled to n = 2*10^6 by
+# the rows processed
 UPDATE_FP64_TRAFFIC = 2 * 686.6e6
 WORKLOAD = "CI-like sparse symmetric n=2,000,000, ~65 nnz/row, k=16 (+5 extra), tol 1e-8"
 # FP64 LOBPCG iterations this workload needs (measured with the GPU FP64 path, which takes

@@ -135,6 +135,8 @@ typedef struct {
   int spmm_variant_fp32;        /* CSR product kernel in use: 0 default, 1 row-parallel,
                                    2 vector gather, 3 band window with global gathers */
   int spmm_variant_fp64;
+  int w_dropped;                /* W columns dropped after an ortho(W~; Y) pass cap (reading R16) */
+  int p_dropped;                /* P columns dropped: x_j did not move (R14) or after a pass cap (R16) */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
@@ -340,7 +342,7 @@ LOBPCG_API lobpcg_status lobpcg_row_norms(int64_t n, const int64_t* row_ptr, con
  * allocator.  The split-row partial sums go to a fixed array in the library,
  * 152 x 1024 doubles (1.2 MB), which every GPU that loads the library holds until the
  * process exits.
- *   n >= 1; 1 <= p, q; p * q <= 1024 (else LOBPCG_EINVAL); X: n x p (ldx), Y: n x q (ldy),
+ *   n >= 1; 1 <= p, q <= 96; p * q <= 1024 (else LOBPCG_EINVAL); X: n x p (ldx), Y: n x q (ldy),
  *   row-major, device; C: device, column-major p x q.
  * The first call on a device looks up that array's device address (cudaGetSymbolAddress)
  * with the device current; make that first call before any stream capture.  All calls

@@ -30,12 +30,13 @@ class _Opts(C.Structure):
 class _Info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("cholqr_passes_max", C.c_int),
                 ("ortho_passes_max", C.c_int), ("shifts", C.c_int), ("svqb", C.c_int),
-                ("cap_hits", C.c_int), ("spmm_columns", C.c_int)]
+                ("cap_hits", C.c_int), ("spmm_columns", C.c_int), ("w_dropped", C.c_int),
+                ("p_dropped", C.c_int)]
 
 
 class _Hist(C.Structure):
     _fields_ = [("cap", C.c_int), ("lambda_", C.c_void_p), ("resnorm", C.c_void_p),
-                ("m_act", C.c_void_p), ("rows", C.c_int)]
+                ("m_act", C.c_void_p), ("rows", C.c_int), ("w_cols", C.c_void_p), ("p_cols", C.c_void_p)]
 
 
 def lib():
@@ -154,6 +155,8 @@ class Result:
     hist_lambda: np.ndarray
     hist_res: np.ndarray
     hist_mact: np.ndarray
+    hist_wcols: np.ndarray
+    hist_pcols: np.ndarray
 
 
 def lobpcg(A, diag, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, maxiter: int = 1000,
@@ -175,12 +178,40 @@ def lobpcg(A, diag, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, m
     hl = np.zeros((cap, m))
     hr = np.zeros((cap, m))
     hm = np.zeros(cap, dtype=np.int32)
-    hist = _Hist(cap, _p(hl), _p(hr), _p(hm), 0)
+    hw = np.zeros(cap, dtype=np.int32)
+    hp = np.zeros(cap, dtype=np.int32)
+    hist = _Hist(cap, _p(hl), _p(hr), _p(hm), 0, _p(hw), _p(hp))
     st = lib().oracle_lobpcg(C.byref(op.s), _p(d), C.byref(opts), _p(X0), _p(evals), _p(evecs),
                              _p(res), C.byref(info), C.byref(hist))
     info_d = {f: getattr(info, f) for f, _ in _Info._fields_}
     r = hist.rows
-    return Result(st, evals, evecs, res, info_d, hl[:r], hr[:r], hm[:r])
+    return Result(st, evals, evecs, res, info_d, hl[:r], hr[:r], hm[:r], hw[:r], hp[:r])
+
+
+def precondition(R: np.ndarray, lam: np.ndarray, diag: np.ndarray, m_conv: int, m_act: int,
+                 precond: int = 1) -> np.ndarray:
+    """W~ = T R over the active columns m_conv .. m_conv + m_act - 1 (reading R6)."""
+    R = _f64(R)
+    n = R.shape[0]
+    lam = np.ascontiguousarray(lam, dtype=np.float64)
+    diag = np.ascontiguousarray(diag, dtype=np.float64)
+    W = np.zeros((n, max(m_act, 1)), order="F")
+    lib().oracle_precondition(C.c_int64(n), C.c_int(m_conv), C.c_int(m_act), _p(R), _p(lam), _p(diag),
+                              C.c_int(precond), _p(W))
+    return W[:, :m_act]
+
+
+def drop_unorthogonal_columns(W: np.ndarray, Y: np.ndarray | None, tau: float = 1e-14,
+                              check_norm: bool = True) -> np.ndarray:
+    """Reading R16: the columns of W kept (packed, in order)."""
+    W = _f64(W)
+    n, p = W.shape
+    q = 0 if Y is None else Y.shape[1]
+    Yf = None if Y is None else _f64(Y)
+    lib().oracle_drop_unorthogonal_columns.restype = C.c_int
+    kept = lib().oracle_drop_unorthogonal_columns(C.c_int64(n), C.c_int(p), _p(W), C.c_int(q), _p(Yf),
+                                                  C.c_double(tau), C.c_int(1 if check_norm else 0))
+    return W[:, :kept]
 
 
 def threads() -> int:

@@ -45,14 +45,21 @@
  *      whose norm is at the rounding level of the others is still normalised.  Without
  *      it such a column (a P direction of a Ritz vector that did not move) stays
  *      unnormalised through every pass and breaks the orthonormality of V.
- *  R16 When ortho(W~; Y) stops at its pass cap, the columns of W whose largest overlap
- *      with Y is still above sqrt(tau) are dropped from W (W then has fewer than m_act
- *      columns).  Such a column's direction was (to rounding) already in span(Y), so
- *      the search space loses nothing; kept, it would make V rank-deficient and give a
- *      spurious Ritz value with a vanishing vector.  The same rule, plus a unit-norm
- *      check, is applied to u_p in R^s: when a column was unlocked since the previous
- *      step, more P directions are asked for than the complement of u_x in R^s holds
- *      (s - m of them), and the surplus column cannot be made orthogonal.
+ *  R16 Algorithm 3 (and the Algorithm 2 inside it) may stop at a pass cap without having
+ *      produced orthonormal columns orthogonal to Y.  Only then (a cap was hit during
+ *      the call) are the columns whose largest overlap with Y is above sqrt(tau), or
+ *      whose norm differs from 1 by more than sqrt(tau), dropped; the kept columns are
+ *      packed to the front in their order.  When no cap is hit every column passed the
+ *      tau tests and the rule cannot fire, so it never changes a run in which the
+ *      paper's loops succeed.  It differs from dropping ill-conditioned directions
+ *      during the orthogonalisation (Sec. 1, Duersch et al.): nothing is dropped while
+ *      the shifted Cholesky-QR still works, only directions the loops could not make
+ *      part of an orthonormal basis.  The cases that reach it are degenerate: a W~
+ *      column that is exactly zero (an active pair whose residual is exactly zero; its
+ *      direction is already in X), more columns than the complement of Y holds (u_p in
+ *      R^s after a column was unlocked: s - m directions for a_act columns), both
+ *      applied to W (n rows) and to u_p (s rows).  Kept, such a column would make V
+ *      rank-deficient and give a spurious Ritz value with a vanishing vector.
  *  R14 A P direction exists only where x_j moved: the coefficient vector u~_p of column j,
  *      after projecting out u_x, is (I - u_x u_x^T) e_j; when it vanishes exactly (norm
  *      <= 1e-200, e.g. when the Rayleigh-Ritz coupling of a localised vector is exactly
@@ -377,17 +384,18 @@ int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, do
   return passes;
 }
 
-/* R16: after ortho(W~; Y), drop the columns of W whose overlap with Y is still above
- * sqrt(tau) (and, with check_norm, whose norm is not 1 to sqrt(tau)); the kept columns
- * are packed to the front.  Returns their number. */
-static int drop_unorthogonal_columns(int64_t n, int p, double* W, int q, const double* Y, double tau,
+/* R16: drop the columns of W whose overlap with Y is above sqrt(tau) (and, with
+ * check_norm, whose norm is not 1 to sqrt(tau)); the kept columns are packed to the
+ * front in their order.  Returns their number.  Algorithm 1 calls it only after an
+ * Algorithm 2/3 pass cap was hit. */
+int oracle_drop_unorthogonal_columns(int64_t n, int p, double* W, int q, const double* Y, double tau,
                                      int check_norm) {
-  if (q <= 0 || p <= 0) return p;
-  double* Cm = (double*)malloc(sizeof(double) * (size_t)q * p);
-  oracle_gram(n, q, Y, p, W, Cm);
+  if (p <= 0) return 0;
+  double* Cm = (double*)malloc(sizeof(double) * (size_t)(q > 0 ? q : 1) * p);
+  if (q > 0) oracle_gram(n, q, Y, p, W, Cm);
   int kept = 0;
   for (int j = 0; j < p; ++j) {
-    const double worst = max_abs(q, Cm + (size_t)j * q);
+    const double worst = q > 0 ? max_abs(q, Cm + (size_t)j * q) : 0.0;
     const double nrm = sqrt(pairwise_dot(W + (size_t)j * n, W + (size_t)j * n, n));
     if (worst <= sqrt(tau) && (!check_norm || fabs(nrm - 1.0) <= sqrt(tau))) {
       if (kept != j) memcpy(W + (size_t)kept * n, W + (size_t)j * n, sizeof(double) * n);
@@ -422,8 +430,13 @@ static void residuals(int64_t n, int m, const double* X, const double* AX, const
     conv[j] = column_converged(n, R + (int64_t)j * n, tol, tol_kind, &nrm[j]);
 }
 
-static void record(oracle_history* h, int m, const double* lam, const double* nrm, int m_act) {
+/* Row t of the history: Ritz values and residual norms after Rayleigh-Ritz step t, the
+ * active count that follows, and the widths of W and P in the basis of that step. */
+static void record(oracle_history* h, int m, const double* lam, const double* nrm, int m_act, int w_cols,
+                   int p_cols) {
   if (!h || h->rows >= h->cap) return;
+  if (h->w_cols) h->w_cols[h->rows] = w_cols;
+  if (h->p_cols) h->p_cols[h->rows] = p_cols;
   if (h->lambda) memcpy(h->lambda + (size_t)h->rows * m, lam, sizeof(double) * (size_t)m);
   if (h->resnorm) memcpy(h->resnorm + (size_t)h->rows * m, nrm, sizeof(double) * (size_t)m);
   if (h->m_act) h->m_act[h->rows] = m_act;
@@ -431,7 +444,7 @@ static void record(oracle_history* h, int m, const double* lam, const double* nr
 }
 
 /* Precondition the active residual columns (R6): W~ = T R[:, act]. */
-static void precondition(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+void oracle_precondition(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
                          const double* diag, int precond, double* W) {
   for (int c = 0; c < m_act; ++c) {
     int j = m_conv + c;
@@ -526,19 +539,21 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
   int m_conv = 0;
   while (m_conv < m && conv[m_conv]) ++m_conv;                            /* R1, R7 */
   int m_act = m - m_conv;
-  record(hist, m, lam, nrm, m_act);
+  record(hist, m, lam, nrm, m_act, 0, 0);
   int have_p = 0, it = 0;
   if (m_conv >= k) {
     status = ORACLE_OK;
     goto done;
   }
-  precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);          /* W~ = T R */
+  oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);          /* W~ = T R */
   int w_cols = m_act; /* columns of W (R16) */
   {
+    const int hits0 = loc.cap_hits;
     int p2 = oracle_ortho_against(n, m_act, W, m, X, tau, cap, cap2, &loc.shifts, &loc.svqb,
                                   &loc.cap_hits, &loc.cholqr_passes_max); /* W = ortho(W~; X) */
     if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;
-    w_cols = drop_unorthogonal_columns(n, m_act, W, m, X, tau, 0);
+    if (loc.cap_hits > hits0) w_cols = oracle_drop_unorthogonal_columns(n, m_act, W, m, X, tau, 1); /* R16 */
+    loc.w_dropped += m_act - w_cols;
   }
   oracle_apply(A, w_cols, W, AW);                                         /* AW = A W */
   loc.spmm_columns += w_cols;
@@ -567,7 +582,7 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     m_conv = 0;
     while (m_conv < m && conv[m_conv]) ++m_conv;                          /* lock, R7 */
     m_act = m - m_conv;
-    record(hist, m, lam, nrm, m_act);
+    record(hist, m, lam, nrm, m_act, w_cols, have_p);
     if (m_conv >= k) {
       status = ORACLE_OK;
       break;
@@ -592,23 +607,30 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
       free(proj);
       if (sqrt(nrm) > 1e-200) ++p_cols;
     }
+    loc.p_dropped += m_act - p_cols; /* R14 */
     if (p_cols > 0) {
+      const int hits0 = loc.cap_hits, asked = p_cols;
       int p2 = oracle_ortho_against(s, p_cols, up, m, U, tau, cap, cap2, &loc.shifts,
                                     &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
       (void)p2;
-      p_cols = drop_unorthogonal_columns(s, p_cols, up, m, U, tau, 1); /* R16 in R^s */
+      if (loc.cap_hits > hits0) p_cols = oracle_drop_unorthogonal_columns(s, p_cols, up, m, U, tau, 1); /* R16 in R^s */
+      loc.p_dropped += asked - p_cols;
     }
     block_times_small(n, s, V, p_cols, up, P);                            /* P = V u_p, AP = AV u_p */
     block_times_small(n, s, AV, p_cols, up, AP);
     have_p = p_cols;
-    precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
+    oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
     memcpy(Y, X, sizeof(double) * n * m);                                 /* Y = (X, P) */
     memcpy(Y + n * m, P, sizeof(double) * n * have_p);
     {
+      const int hits0 = loc.cap_hits;
       int p2 = oracle_ortho_against(n, m_act, W, m + have_p, Y, tau, cap, cap2, &loc.shifts,
                                     &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
       if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;           /* W = ortho(W~; (X, P)) */
-      w_cols = drop_unorthogonal_columns(n, m_act, W, m + have_p, Y, tau, 0); /* R16 */
+      w_cols = m_act;
+      if (loc.cap_hits > hits0)
+        w_cols = oracle_drop_unorthogonal_columns(n, m_act, W, m + have_p, Y, tau, 1); /* R16 */
+      loc.w_dropped += m_act - w_cols;
     }
     oracle_apply(A, w_cols, W, AW);                                       /* AW = A W */
     loc.spmm_columns += w_cols;

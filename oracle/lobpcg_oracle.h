@@ -48,6 +48,8 @@ typedef struct {
   int svqb;              /* SVQB fallbacks, summed over the run */
   int cap_hits;          /* ortho loops that stopped at their pass cap */
   int spmm_columns;      /* columns multiplied by A, summed over the run */
+  int w_dropped;         /* W columns dropped by R16, summed over the run */
+  int p_dropped;         /* P columns dropped by R14 (x_j did not move) or R16, summed */
 } oracle_info;
 
 /* Per-iteration history (optional; any pointer may be NULL).  Row t (t = 0 is the
@@ -58,6 +60,8 @@ typedef struct {
   double* resnorm;  /* cap x m, row-major */
   int* m_act;       /* cap */
   int rows;         /* rows written */
+  int* w_cols;      /* cap: columns of W in the basis of step t (0 for the initial step) */
+  int* p_cols;      /* cap: columns of P in the basis of step t */
 } oracle_history;
 
 enum { ORACLE_OK = 0, ORACLE_EINVAL = 1, ORACLE_ENOMEM = 2, ORACLE_ENOCONV = 4, ORACLE_EBREAKDOWN = 5 };
@@ -91,6 +95,18 @@ int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, 
 int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, double tau,
                          int cap, int cap2, int* shifts, int* svqb, int* cap_hit,
                          int* cholqr_passes_max);
+
+/* Diagonal preconditioner of Sec. 2 on the active residual columns (reading R6):
+ * W[:, c] = R[:, m_conv + c] / delta, delta = diag - lam[m_conv + c] guarded away from zero;
+ * precond == 0 copies R.  R: n x m, W: n x m_act, column-major. */
+void oracle_precondition(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+                         const double* diag, int precond, double* W);
+
+/* Reading R16: drop the columns of W (n x p) whose largest |overlap| with Y (n x q) is
+ * above sqrt(tau), and with check_norm those whose 2-norm differs from 1 by more than
+ * sqrt(tau); kept columns are packed to the front in order.  Returns their number. */
+int oracle_drop_unorthogonal_columns(int64_t n, int p, double* W, int q, const double* Y, double tau,
+                                     int check_norm);
 
 /* Algorithm 1.  diag = diag(A) (length n).  X0 = n x m initial block (m = k + extra),
  * required.  Outputs: evals (k), evecs (n x k column-major), resnorms (k) = ||A x_j -

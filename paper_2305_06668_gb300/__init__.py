@@ -53,7 +53,8 @@ class _Info(C.Structure):
                 ("phase_seconds_fp64", C.c_double * 6), ("spmm_launches_fp64", C.c_int64),
                 ("spmm_columns_fp64", C.c_int64), ("update_fp64_seconds", C.c_double),
                 ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64),
-                ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int)]
+                ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int), ("w_dropped", C.c_int),
+                ("p_dropped", C.c_int)]
 
 
 def library_path() -> pathlib.Path:

@@ -195,8 +195,8 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t n, UpdateJob<T> job
         for (int j = 0; j < CJ; ++j) {
           const int col = cj * CJ + j;
           if (col < q) {
-            const double rij = (double)(res[1][j] - (T)lam[col] * res[0][j]);
-            nsum[j] += rij * rij;
+            const double rij = (double)fma(-(T)lam[col], res[0][j], res[1][j]);  // AX - lam X, one rounding
+            nsum[j] = fma(rij, rij, nsum[j]);
             nmax[j] = fmax(nmax[j], fabs(rij));
           }
         }

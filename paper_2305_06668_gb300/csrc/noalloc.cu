@@ -50,6 +50,10 @@ extern "C" lobpcg_status lobpcg_gram_f64_noalloc(int64_t n, int p, const double*
     set_thread_error("lobpcg_gram_f64_noalloc: need n >= 1, p, q >= 1, ld >= width and non-NULL arrays");
     return LOBPCG_EINVAL;
   }
+  if (p > kMaxS || q > kMaxS) {
+    set_thread_error("lobpcg_gram_f64_noalloc: p and q must be <= 96 (widest Gram the kernels take)");
+    return LOBPCG_EINVAL;
+  }
   if ((int64_t)p * q > kMaxEntries) {
     set_thread_error("lobpcg_gram_f64_noalloc: p * q must be <= 1024 (size of the fixed scratch array)");
     return LOBPCG_EINVAL;

@@ -84,6 +84,7 @@ struct Stats {
   int64_t spmm_launches64 = 0, spmm_columns64 = 0;
   int precond_fallback = 0;
   int w_dropped = 0;
+  int p_dropped = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -445,15 +446,17 @@ int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap) {
 }
 
 // Algorithm 3: W (n x p) <- ortho(W; Y), Y orthonormal (Cols).  Body runs at least once.
-// If the pass cap stops it with columns still overlapping Y by more than sqrt(tau), those
-// columns are dropped and the rest packed to the front (reading R16); *kept receives the
-// number of columns left (p otherwise).
+// Reading R16: when a pass cap (of Algorithm 3 or of an Algorithm 2 inside it) was hit,
+// the columns whose overlap with Y is above sqrt(tau) or whose norm differs from 1 by more
+// than sqrt(tau) are dropped and the rest packed to the front in order; *kept receives the
+// number of columns left (p otherwise).  Without a cap hit no column can fail these tests.
 template <class T>
 int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double tau, int cap, int cap2,
                   int* kept = nullptr) {
   if (kept) *kept = p;
   if (p <= 0) return 0;
   const int q = Y.width();
+  const int hits0 = c.stats.cap_hits;
   int passes = 0;
   double last = 0.0;
   bool c_ready = false;  // C = Y^T W of the current W is already in c.C (the previous pass's test)
@@ -485,17 +488,21 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
     }
     c_ready = true;
   }
-  if (q > 0 && kept && !(last <= std::sqrt(tau))) {
-    // R16: keep the columns whose overlap with Y is at most sqrt(tau)
-    std::vector<double> Ch((size_t)q * p);
-    LB_CUDA(cudaMemcpyAsync(Ch.data(), c.C, Ch.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+  if (kept && c.stats.cap_hits > hits0) {
+    // R16: c.C holds Y^T W of the final W (the last pass's test); the norms come from W^T W
+    const Cols<T> w = cols1<T>(W, ld, p);
+    gram<T>(c, w, w, false, c.G);
+    std::vector<double> Ch((size_t)q * p), Mh((size_t)p * p);
+    if (q > 0) LB_CUDA(cudaMemcpyAsync(Ch.data(), c.C, Ch.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    LB_CUDA(cudaMemcpyAsync(Mh.data(), c.G, Mh.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
     c.sync();
     std::vector<double> sel((size_t)p * p, 0.0);  // p x p column selection (column-major)
     int k2 = 0;
     for (int j = 0; j < p; ++j) {
       double worst = 0.0;
       for (int i = 0; i < q; ++i) worst = std::max(worst, std::fabs(Ch[(size_t)j * q + i]));
-      if (worst <= std::sqrt(tau)) sel[(size_t)k2 * p + j] = 1.0, ++k2;  // W is unit after Algorithm 2
+      const double nrm = std::sqrt(std::max(Mh[(size_t)j * p + j], 0.0));
+      if (worst <= std::sqrt(tau) && std::fabs(nrm - 1.0) <= std::sqrt(tau)) sel[(size_t)k2 * p + j] = 1.0, ++k2;
     }
     if (k2 < p) {
       LB_CUDA(cudaMemcpyAsync(c.Tm, sel.data(), sel.size() * sizeof(double), cudaMemcpyHostToDevice, c.st));
@@ -695,6 +702,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     m_conv = ls.m_conv;
     c.prof.mark(PH_UPDATE);
     const int pw_new = ls.p_cols;  // P directions whose Ritz vector moved (reading R14)
+    c.stats.p_dropped += a_new - pw_new;
     if (pw_new > 0) {
       UpdateJob<T> pj{};
       pj.in[0] = V, pj.in[1] = AV;
@@ -989,6 +997,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->update_fp64_launches = c->prof.on ? (int64_t)(c->prof.kused / 2) : 0;
       info->spmm_variant_fp32 = c->var32;
       info->spmm_variant_fp64 = c->var64;
+      info->w_dropped = c->stats.w_dropped;
+      info->p_dropped = c->stats.p_dropped;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))

@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(256) update_row_kernel(int64_t n, UpdateJob<T>
 #pragma unroll
       for (int j = 0; j < QMAX; ++j) {
         if (j < q) {
-          const T rij = res[1][j] - (T)lam[j] * res[0][j];
+          const T rij = fma(-(T)lam[j], res[0][j], res[1][j]);  // AX - lam X, one rounding
           nsum[j] = fma(rij, rij, nsum[j]);
           nmax[j] = fmax(nmax[j], fabs(rij));
         }

@@ -343,3 +343,30 @@ def test_update_f32_matches_oracle(n, ws, ld, q, mode):
     else:
         X = lb.update_f32(Vd, Ud)
         assert np.all(np.abs(X.cpu().numpy().astype(np.float64) - ref) <= tol)
+
+
+def test_update_f32_staged_and_general_layouts_agree():
+    """The staged kernel (16-byte rows, ld a multiple of 4) and the general-layout kernel
+    (here ld = 23) run the same FMA chain per element and form the residual AX - lam X
+    with one fused multiply-add, so X and AX agree bit for bit and the residual norms
+    differ only by the order of the per-row partial sums."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    n, ws, q = 70_001, [21, 21, 21], 21
+    s = sum(ws)
+    Vs = [synth.gaussian_block(n, w, seed=300 + i).astype(np.float32) for i, w in enumerate(ws)]
+    AVs = [synth.gaussian_block(n, w, seed=400 + i).astype(np.float32) for i, w in enumerate(ws)]
+    U = torch.from_numpy(synth.gaussian_block(s, q, seed=8) / np.sqrt(s)).cuda()
+    lam = torch.from_numpy(np.linspace(-1.0, 2.0, q)).cuda()
+    out = {}
+    for ld in (24, 23):
+        def block32(M):
+            buf = torch.zeros((n, ld), dtype=torch.float32, device="cuda")
+            buf[:, :M.shape[1]] = torch.from_numpy(M).cuda()
+            return buf[:, :M.shape[1]]
+        zero = np.zeros((n, q), dtype=np.float32)
+        X, AX, rn = lb.update_f32([block32(M) for M in Vs], U, AV=[block32(M) for M in AVs], lam=lam,
+                                  X=block32(zero), AX=block32(zero), resnorm=True)
+        out[ld] = (X.cpu().numpy(), AX.cpu().numpy(), np.asarray(rn))
+    assert np.array_equal(out[24][0], out[23][0]) and np.array_equal(out[24][1], out[23][1])
+    assert np.all(np.abs(out[24][2] - out[23][2]) <= 1e-6 * out[24][2])

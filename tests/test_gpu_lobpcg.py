@@ -179,3 +179,19 @@ def test_autotuned_products_give_the_same_eigenpairs(precision):
     assert 0 <= r1.info["spmm_variant_fp64"] <= 3 and 0 <= r1.info["spmm_variant_fp32"] <= 3
     assert np.max(rel_eig_err(r1.evals, r0.evals)) <= 1e-10
     assert np.max(r1.resnorms) <= 1e-8
+
+
+def test_exact_active_pair_drops_like_the_oracle():
+    """An exact eigenvector behind an unconverged pair: its W~ column is exactly zero and its
+    Ritz vector does not move, so readings R16 (drop the W column Algorithm 2 cannot
+    normalise) and R14 (no P direction) fire on both sides; the results are exact."""
+    torch = cuda()
+    from tests.test_oracle_rules import _exact_pair_problem
+    A, d, X0 = _exact_pair_problem()
+    ref = oracle.lobpcg(A, d, 2, X0, tol=1e-10, maxiter=200)
+    res = _solve(torch, None, 2, X0, dense=A, tol=1e-10, maxiter=200)
+    assert ref.status == 0 and res.status == 0
+    _parity(res, ref)
+    assert np.max(np.abs(res.evals - [1.0, 2.0])) <= 1e-14
+    assert res.info["w_dropped"] == ref.info["w_dropped"] >= 1
+    assert res.info["p_dropped"] == ref.info["p_dropped"] >= 1

@@ -42,3 +42,9 @@ def test_noalloc_gram_rejects_sizes_beyond_its_array():
     with pytest.raises(lb.LobpcgError) as e:
         lb.gram_noalloc(X, Y)
     assert e.value.status == lb.EINVAL and "1024" in str(e.value)
+    # within p * q <= 1024 but wider than the Gram kernels take: also an argument error
+    X1 = dev(torch, synth.gaussian_block(100, 1, seed=3))
+    Y100 = dev(torch, synth.gaussian_block(100, 100, seed=4))
+    with pytest.raises(lb.LobpcgError) as e:
+        lb.gram_noalloc(X1, Y100)
+    assert e.value.status == lb.EINVAL and "96" in str(e.value)
