@@ -35,12 +35,11 @@ N_ROWS, K, EXTRA, TOL, SEED = 2_000_000, 16, 5, 1e-8, 0
 # the rows processed
 UPDATE_FP64_TRAFFIC = 2 * 686.6e6
 WORKLOAD = "CI-like sparse symmetric n=2,000,000, ~65 nnz/row, k=16 (+5 extra), tol 1e-8"
-# FP64 LOBPCG iterations this workload needs (measured with the GPU FP64 path, which takes
-# the same steps as the oracle); scales the oracle's per-iteration time of the reference arm.
-FP64_ITERATIONS_FALLBACK = 1500
-# FP64 FMA throughput of this part, measured with a DFMA loop on all 152 SMs (2 FMA per
-# clock per SM at ~1.9-2.0 GHz); the peak for FP64-bound kernels.
-FP64_PEAK_TFLOPS = 1.20
+# Record of one complete oracle solve of this workload (iterations, wall time, threads, the
+# per-iteration time of its first iterations), written by oracle/record_full_solve.py, which
+# calls only the oracle.  Both CPU legs scale it to the machine's cores.
+ORACLE_RECORD = os.path.join(ROOT, "oracle", "records", "ci2m_seed0.json")
+FP64_PEAK_SOURCE = "FP64 FMA rate measured in this run (lobpcg_probe_fma_rate)"
 
 
 def log(*a):
@@ -125,51 +124,76 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def cpu_baseline(a, x0, iters_to_solution: int, max_seconds: float = 30.0):
-    """The oracle, as it stands, on a bounded sample: the initialisation plus two
-    iterations of the full-size workload; scaled to a whole solve by the iteration count."""
+def oracle_sample(a, x0):
+    """Bounded sample of the oracle, as it stands, on the full workload: its initialisation
+    alone, then the initialisation plus two iterations (about 10 s of CPU work)."""
     import oracle
+    oracle.lib()
     t0 = time.perf_counter()
-    oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=1, hist_cap=4)
+    oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=0, hist_cap=2)
     t1 = time.perf_counter()
-    oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=3, hist_cap=4)
+    oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=2, hist_cap=4)
     t2 = time.perf_counter()
-    per_it = max((t2 - t1) - (t1 - t0), 1e-9) / 2.0
-    init = max((t1 - t0) - per_it, 0.0)
-    return {"value": init + iters_to_solution * per_it, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
-            "sample": f"oracle init + 1 and init + 3 iterations on the full n={N_ROWS} workload "
-                      f"({t2 - t0:.1f} s of CPU work); per-iteration time {per_it:.2f} s x {iters_to_solution} "
-                      f"FP64 iterations + init {init:.2f} s"}
+    init = t1 - t0
+    per_it = max((t2 - t1) - init, 1e-9) / 2.0
+    return init, per_it, t2 - t0
+
+
+def oracle_time_to_solution(a, x0):
+    """The one formula of both CPU legs: the oracle's time to the k pairs on this machine.
+
+    A complete oracle solve of the workload is too long for a benchmark run, so it is
+    extrapolated from a measured sample.  With the record of a complete oracle solve (its
+    wall time T_rec and the per-iteration time p_rec of its first iterations, on the cores
+    where it ran), the estimate is T_rec * p / p_rec, p the per-iteration time measured
+    here: the record carries the oracle's own iteration count and the shrinking active
+    block of soft locking.  Without a record: init + iterations x p at the full width."""
+    import oracle
+    init, per_it, spent = oracle_sample(a, x0)
+    cores = oracle.threads()
+    rec = None
+    try:
+        with open(ORACLE_RECORD) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        rec = None
+    if rec and rec.get("status") == 0:
+        value = rec["seconds"] * per_it / rec["per_iteration_seconds"]
+        sample = (f"extrapolated: oracle init + 2 iterations on the full n={N_ROWS} workload here ({spent:.1f} s of "
+                  f"CPU work, {per_it:.2f} s per iteration on {cores} threads) scaled by the record of a complete "
+                  f"oracle solve ({rec['iterations']} iterations, {rec['seconds']:.0f} s on {rec['threads']} "
+                  f"threads at {rec['per_iteration_seconds']:.2f} s per early iteration)")
+    else:
+        value = None
+        sample = f"no complete oracle solve on record; sample {spent:.1f} s, {per_it:.2f} s per iteration"
+    return {"value": value, "unit": "s", "cores": cores, "kind": "oracle", "extrapolated": True, "sample": sample,
+            "init_seconds": init, "per_iteration_seconds": per_it}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
     a, x0 = make_problem()
-    oracle.lib()
     samples = []
+    est = None
     for step in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=1, hist_cap=4)
-        t1 = time.perf_counter()
+        est = oracle_time_to_solution(a, x0)
         if step >= args.warmup:
-            samples.append(t1 - t0)
-    # each step: initialisation + one iteration of the FP64 oracle on the full workload
-    per_step = statistics.median(samples)
-    t0 = time.perf_counter()
-    oracle.lobpcg(a, a.diag, K, x0, extra=EXTRA, tol=TOL, maxiter=0, hist_cap=2)
-    init = time.perf_counter() - t0
-    per_it = max(per_step - init, 1e-9)
-    value = init + FP64_ITERATIONS_FALLBACK * per_it
+            samples.append((time.perf_counter() - t0, est))
+    per_step = statistics.median(t for t, _ in samples)
+    value = statistics.median(e["value"] for _, e in samples if e["value"] is not None) if est["value"] else None
+    if value is None:
+        print(json.dumps({"impl": "reference", "unavailable": "no complete oracle solve on record to scale"}))
+        return 0
+    base = dict(samples[-1][1])
+    base["value"] = value
     line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
             "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-            "cpu_baseline": {"value": value, "unit": "s", "cores": oracle.threads(), "kind": "oracle",
-                             "sample": f"each step = oracle initialisation + 1 FP64 iteration on the full "
-                                       f"workload ({per_step:.2f} s); scaled by {FP64_ITERATIONS_FALLBACK} iterations"},
+            "cpu_baseline": base,
             "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -186,6 +210,9 @@ def run_ours(args):
     __graft_entry__.build()
     import paper_2305_06668_gb300 as lb
 
+    # FMA-pipe peaks of this GPU, measured now (denominators of the "alu" rooflines)
+    fp64_peak = lb.probe_fma_rate(fp64=True)
+    fp32_peak = lb.probe_fma_rate(fp64=False)
     a, x0_np = make_problem(args.n)
     t = lb.upload_csr(a)
     x0 = torch.from_numpy(x0_np).cuda()
@@ -228,16 +255,31 @@ def run_ours(args):
             print(json.dumps({"profile_run": True, "n": a.n, "s_per_solve": per_solve,
                               "iterations": last["iterations"], "status": [lb.STATUS_NAMES[s] for s in statuses]}))
         return 0
-    # plain FP64 GPU solve of the same problem (the comparison the metric names)
-    fp64 = lb.Solver(**t, extra=EXTRA, precision=lb.FP64, profile=True, maxiter=args.maxiter)
-    r64 = fp64.solve(K, TOL, X0=x0)
+    # the comparison the metric names: plain FP64 GPU solves of the same problem (median of
+    # args.fp64_runs; the iteration count of FP64 LOBPCG on this matrix moves a lot with
+    # rounding), and the two ablations that split the gain into its precision and
+    # preconditioner parts: FP64 + learned, mixed + diagonal
+    def timed_solve(**kw):
+        s = lb.Solver(**t, extra=EXTRA, maxiter=args.maxiter, **kw)
+        rr = s.solve(K, TOL, X0=x0)
+        s.close()
+        return rr
+    plain = [timed_solve(precision=lb.FP64) for _ in range(args.fp64_runs)]
+    r64 = sorted(plain, key=lambda rr: rr.info["seconds"])[len(plain) // 2]
     fp64_time = r64.info["seconds"]
-    fp64.close()
+    ablations = {}
+    for name, kw in (("fp64_learned", dict(precision=lb.FP64, precond=lb.PREC_LEARNED, mlp_weights=weights)),
+                     ("mixed_diagonal", dict(precision=lb.MIXED))):
+        rr = timed_solve(**kw)
+        ablations[name] = {"seconds": rr.info["seconds"], "iterations": rr.info["iterations"],
+                           "fp64_iterations": rr.info["fp64_iterations"], "status": lb.STATUS_NAMES[rr.status],
+                           "max_resnorm": float(np.max(rr.resnorms)),
+                           "eig_max_rel_diff_vs_fp64": float(np.max(np.abs(rr.evals - r64.evals) /
+                                                                    np.maximum(1, np.abs(r64.evals))))}
 
     # rooflines of the main kernels from the phase timings of the timed solves (CUDA
     # events on the solver stream); the dominant phase's is reported as "roofline"
     hbm_peak, peak_kind = measured_peaks()
-    fp64_peak = FP64_PEAK_TFLOPS
     tot = lambda key, ph: sum(i[key][ph] for _, i, _, _ in infos)
     ph_all = {ph: tot("phase_seconds", ph) for ph in lb.PHASES}
     ph64 = {ph: tot("phase_seconds_fp64", ph) for ph in lb.PHASES}
@@ -266,7 +308,7 @@ def run_ours(args):
                                   "achieved": f64 / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                                   "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
                                   "flops_per_launch": f64, "avg_launch_s": t64,
-                                  "peak_source": "FP64 FMA rate measured on this GB300 (probe, 1.19-1.20 TFLOP/s)"}
+                                  "peak_source": FP64_PEAK_SOURCE}
     # the FP64 block update (update_kernel<double>): the kernel with the largest share of GPU
     # time in the ncu launch list of this command, timed per launch with CUDA events
     ut = sum(i["update_fp64_seconds"] for _, i, _, _ in infos)
@@ -278,7 +320,7 @@ def run_ours(args):
                                     "achieved": uf / ut / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
                                     "frac": uf / ut / 1e12 / fp64_peak, "traffic": UPDATE_FP64_TRAFFIC,
                                     "flops_per_launch": uf / ul, "avg_launch_s": ut / ul,
-                                    "peak_source": "FP64 FMA rate measured on this GB300 (probe, 1.19-1.20 TFLOP/s)"}
+                                    "peak_source": FP64_PEAK_SOURCE}
     share = {k: v / max(sum(ph_all.values()), 1e-30) for k, v in ph_all.items()}
     roofline = dict(rooflines.get("update_fp64", rooflines.get("spmm_fp32", {})))
     roofline["phase_share"] = share
@@ -306,7 +348,7 @@ def run_ours(args):
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        base = cpu_baseline(a, x0_np, r64.info["iterations"])
+        base = oracle_time_to_solution(a, x0_np)
     mixed.close()
     if rank != 0:
         return 0
@@ -322,7 +364,12 @@ def run_ours(args):
             "iterations": last["iterations"], "fp64_iterations": last["fp64_iterations"],
             "max_resnorm": float(infos[-1][2]),
             "fp64_seconds": fp64_time, "fp64_iterations_plain": r64.info["iterations"],
+            "fp64_runs": [{"seconds": rr.info["seconds"], "iterations": rr.info["iterations"],
+                           "status": lb.STATUS_NAMES[rr.status]} for rr in plain],
             "fp64_status": lb.STATUS_NAMES[r64.status], "speedup_vs_fp64": fp64_time / per_solve,
+            "ablations": ablations,
+            "peaks": {"hbm_gbs": hbm_peak, "hbm_source": peak_kind, "fp64_tflops": fp64_peak,
+                      "fp32_tflops": fp32_peak, "fma_source": "lobpcg_probe_fma_rate in this run"},
             "precond_fallback": last["precond_fallback"],
             "eig_max_rel_diff_vs_fp64": float(np.max(np.abs(infos[-1][3] - r64.evals) / np.maximum(1, np.abs(r64.evals)))),
             "phase_seconds_per_solve": {k: v / args.steps for k, v in ph_all.items()},
@@ -409,6 +456,7 @@ def main():
                     help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
     ap.add_argument("--n", type=int, default=N_ROWS, help="rows of the CI-like matrix (profiling runs only)")
     ap.add_argument("--threads", type=int, default=32)
+    ap.add_argument("--fp64-runs", type=int, default=3, help="plain FP64 solves timed (median reported)")
     args = ap.parse_args()
     if args.n != N_ROWS and not args.profile:
         ap.error("--n changes the workload: only for --profile runs")

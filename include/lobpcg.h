@@ -107,6 +107,12 @@ typedef struct {
                                  precision, inside that solve) and keep the fastest.  Meant for
                                  contexts reused over many solves (serving, batches).  0
                                  (default): the built-in choice */
+  int ortho_trim;             /* non-zero (default): the cost trims of Sec. 3.2.  Algorithm 2 skips
+                                 its re-check Gram after an unshifted pass with ||L^-T||_2^2 <= 2
+                                 (bounded from the scaled overlap I + F by 1 / (1 - ||F||_F));
+                                 Algorithm 3 skips its test Gram when eps sqrt(q) times the growth
+                                 factor of ortho (column amplification times that bound) is <=
+                                 tau.  0: the printed Algorithms 2 and 3 */
 } lobpcg_options;
 
 typedef struct {
@@ -137,6 +143,9 @@ typedef struct {
   int spmm_variant_fp64;
   int w_dropped;                /* W columns dropped after an ortho(W~; Y) pass cap (reading R16) */
   int p_dropped;                /* P columns dropped: x_j did not move (R14) or after a pass cap (R16) */
+  int ortho_grams;              /* n-row Gram matrices formed by Algorithms 2 and 3 */
+  int skipped_recheck;          /* Algorithm 2 re-check Grams skipped (ortho_trim) */
+  int skipped_test;             /* Algorithm 3 test Grams skipped (ortho_trim) */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
@@ -352,6 +361,18 @@ LOBPCG_API lobpcg_status lobpcg_row_norms(int64_t n, const int64_t* row_ptr, con
  * the result.  Returns after the stream has finished the work. */
 LOBPCG_API lobpcg_status lobpcg_gram_f64_noalloc(int64_t n, int p, const double* X, int ldx, int q,
                                                  const double* Y, int ldy, double* C, lobpcg_stream stream);
+
+/* ------------------------------------------------------------------------------
+ * Measurement.  The paper has no counterpart: this measures the part the solver runs on.
+ * ------------------------------------------------------------------------------ */
+
+/* Peak rate of the FMA pipes of the current device in TFLOP/s (an FMA counts as 2 flops):
+ * fp64 != 0 measures FP64 fused multiply-adds, fp64 == 0 FP32 ones.  Independent FMA
+ * chains fill every SM; the launch is calibrated to about 50 ms and the best of 5 is
+ * returned in *tflops (host).  This is the denominator of the rooflines of the kernels
+ * bound by the FMA pipes.  Allocates a small output array; synchronises the stream.
+ * EINVAL for a NULL tflops, ECUDA on a CUDA failure. */
+LOBPCG_API lobpcg_status lobpcg_probe_fma_rate(int fp64, double* tflops, lobpcg_stream stream);
 
 #ifdef __cplusplus
 }

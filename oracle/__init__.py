@@ -24,14 +24,21 @@ class _Matrix(C.Structure):
 class _Opts(C.Structure):
     _fields_ = [("k", C.c_int), ("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int),
                 ("precond", C.c_int), ("ortho_cap", C.c_int), ("ortho2_cap", C.c_int),
-                ("tol", C.c_double), ("tau", C.c_double)]
+                ("tol", C.c_double), ("tau", C.c_double), ("trim", C.c_int)]
 
 
 class _Info(C.Structure):
     _fields_ = [("iterations", C.c_int), ("converged", C.c_int), ("cholqr_passes_max", C.c_int),
                 ("ortho_passes_max", C.c_int), ("shifts", C.c_int), ("svqb", C.c_int),
                 ("cap_hits", C.c_int), ("spmm_columns", C.c_int), ("w_dropped", C.c_int),
-                ("p_dropped", C.c_int)]
+                ("p_dropped", C.c_int), ("ortho_grams", C.c_int), ("skipped_recheck", C.c_int),
+                ("skipped_test", C.c_int)]
+
+
+class _OrthoStats(C.Structure):
+    _fields_ = [("passes", C.c_int), ("grams", C.c_int), ("shifts", C.c_int), ("svqb", C.c_int),
+                ("cap_hits", C.c_int), ("cholqr_passes_max", C.c_int), ("skipped_recheck", C.c_int),
+                ("skipped_test", C.c_int)]
 
 
 class _Hist(C.Structure):
@@ -124,25 +131,29 @@ def svqb(X: np.ndarray) -> np.ndarray:
     return X
 
 
-def ortho(X: np.ndarray, tau: float = 1e-14, cap: int = 6):
-    """Algorithm 2.  Returns (Q, stats)."""
+def ortho(X: np.ndarray, tau: float = 1e-14, cap: int = 6, trim: bool = True):
+    """Algorithm 2 (with trim: the re-check skip of reading R17).  Returns (Q, stats)."""
     X = _f64(X)
-    sh, sv, ch, pm = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
-    passes = lib().oracle_ortho(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X), C.c_double(tau),
-                                C.c_int(cap), C.byref(sh), C.byref(sv), C.byref(ch), C.byref(pm))
-    return X, dict(passes=passes, shifts=sh.value, svqb=sv.value, cap_hits=ch.value)
+    st = _OrthoStats()
+    passes = lib().oracle_ortho_ex(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X), C.c_double(tau),
+                                   C.c_int(cap), C.c_int(1 if trim else 0), C.byref(st))
+    d = {f: getattr(st, f) for f, _ in _OrthoStats._fields_}
+    d["passes"] = passes
+    return X, d
 
 
-def ortho_against(X: np.ndarray, Y: np.ndarray, tau: float = 1e-14, cap: int = 6, cap2: int = 4):
-    """Algorithm 3.  Returns (Q, stats)."""
+def ortho_against(X: np.ndarray, Y: np.ndarray, tau: float = 1e-14, cap: int = 6, cap2: int = 4,
+                  trim: bool = True):
+    """Algorithm 3 (with trim: readings R17 and R18).  Returns (Q, stats)."""
     X = _f64(X)
     Y = _f64(Y)
-    sh, sv, ch, pm = C.c_int(0), C.c_int(0), C.c_int(0), C.c_int(0)
-    passes = lib().oracle_ortho_against(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X),
-                                        C.c_int(Y.shape[1]), _p(Y), C.c_double(tau), C.c_int(cap),
-                                        C.c_int(cap2), C.byref(sh), C.byref(sv), C.byref(ch), C.byref(pm))
-    return X, dict(passes=passes, shifts=sh.value, svqb=sv.value, cap_hits=ch.value,
-                   cholqr_passes_max=pm.value)
+    st = _OrthoStats()
+    passes = lib().oracle_ortho_against_ex(C.c_int64(X.shape[0]), C.c_int(X.shape[1]), _p(X),
+                                           C.c_int(Y.shape[1]), _p(Y), C.c_double(tau), C.c_int(cap),
+                                           C.c_int(cap2), C.c_int(1 if trim else 0), C.byref(st))
+    d = {f: getattr(st, f) for f, _ in _OrthoStats._fields_}
+    d["passes"] = passes
+    return X, d
 
 
 @dataclasses.dataclass
@@ -161,15 +172,17 @@ class Result:
 
 def lobpcg(A, diag, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, maxiter: int = 1000,
            tol_kind: int = 0, precond: int = 1, tau: float = 1e-14, ortho_cap: int = 6,
-           ortho2_cap: int = 4, hist_cap: int | None = None) -> Result:
-    """Algorithm 1 on a CSR (synth.CSR) or dense (ndarray) symmetric matrix."""
+           ortho2_cap: int = 4, hist_cap: int | None = None, trim: bool = True) -> Result:
+    """Algorithm 1 on a CSR (synth.CSR) or dense (ndarray) symmetric matrix.  trim: the cost
+    trims of Sec. 3.2 (readings R17, R18), as in the GPU library's default; False runs the
+    printed Algorithms 2 and 3."""
     op = _operator(A)
     n = op.n
     m = k + extra
     X0 = _f64(X0)
     assert X0.shape == (n, m), (X0.shape, n, m)
     d = None if diag is None else np.ascontiguousarray(diag, dtype=np.float64)
-    opts = _Opts(k, extra, maxiter, tol_kind, precond, ortho_cap, ortho2_cap, tol, tau)
+    opts = _Opts(k, extra, maxiter, tol_kind, precond, ortho_cap, ortho2_cap, tol, tau, 1 if trim else 0)
     evals = np.zeros(k)
     evecs = np.zeros((n, k), order="F")
     res = np.zeros(k)

@@ -307,17 +307,29 @@ void oracle_svqb(int64_t n, int p, double* X, const double* M) {
   free(dmd), free(Z), free(th), free(Dv), free(T), free(Xc);
 }
 
-int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, int* svqb,
-                 int* cap_hit, int* passes_max) {
+/* Algorithm 2.  With trim (Sec. 3.2, the estimate of ||L^{-T}|| that makes the final
+ * re-check unnecessary, reading R17): after an unshifted pass whose scaled overlap
+ * S = D M D = I + F has ||F||_F <= 1/2, ||L^{-T}||_2^2 = 1 / lambda_min(S) <= 1 / (1 - ||F||_F)
+ * <= 2, so the new vectors are orthonormal to about twice the Gram's rounding and the
+ * loop ends without forming X^T X again.  d2_first (nullable, p) receives diag of the
+ * first X^T X (the squared input column norms) and *l2_first the bound on
+ * ||L^{-T}||_2^2 of the first pass (1 when no pass was needed, HUGE_VAL after a shift or
+ * an SVQB step): the error amplification Algorithm 3's growth factor needs. */
+static int ortho_impl(int64_t n, int p, double* X, double tau, int cap, int trim, oracle_ortho_stats* st,
+                      double* d2_first, double* l2_first) {
+  if (l2_first) *l2_first = 1.0;
   if (p <= 0) return 0;
   double* M = (double*)malloc(sizeof(double) * (size_t)p * p);
   double* L = (double*)malloc(sizeof(double) * (size_t)p * p);
   int passes = 0;
+  oracle_gram(n, p, X, p, X, M); /* M = X^T X */
+  st->grams++;
+  if (d2_first)
+    for (int j = 0; j < p; ++j) d2_first[j] = M[j + j * p];
   for (;;) {
-    oracle_gram(n, p, X, p, X, M); /* M = X^T X */
     if (max_abs_minus_identity(p, M) <= tau) break;
     if (passes >= cap) {
-      if (cap_hit) ++*cap_hit;
+      st->cap_hits++;
       break;
     }
     ++passes;
@@ -327,8 +339,16 @@ int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, 
     for (int i = 0; i < p; ++i) Dv[i] = M[i + i * p] > 0.0 ? 1.0 / sqrt(M[i + i * p]) : 1.0;
     for (int j = 0; j < p; ++j)
       for (int i = 0; i < p; ++i) Ms[i + j * p] = Dv[i] * M[i + j * p] * Dv[j];
+    double fro_off = 0.0; /* ||F||_F, F = S - I */
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i) {
+        const double f = Ms[i + j * p] - (i == j ? 1.0 : 0.0);
+        fro_off += f * f;
+      }
+    fro_off = sqrt(fro_off);
     memcpy(L, Ms, sizeof(double) * (size_t)p * p);
     int fail = oracle_cholesky(p, L);
+    const int shifted = fail != 0;
     if (fail) {
       /* level shift (Sec. 3.2), grown by 10x until the factorisation succeeds */
       double tr = 0.0;
@@ -337,51 +357,126 @@ int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, 
       for (int t = 0; t < 8 && fail; ++t, sigma *= 10.0) {
         memcpy(L, Ms, sizeof(double) * (size_t)p * p);
         for (int i = 0; i < p; ++i) L[i + i * p] += sigma;
-        if (shifts) ++*shifts;
+        st->shifts++;
         fail = oracle_cholesky(p, L);
       }
     }
     free(Ms);
+    if (passes == 1 && l2_first) *l2_first = (!shifted && fro_off < 1.0) ? 1.0 / (1.0 - fro_off) : HUGE_VAL;
     if (fail) {
       free(Dv);
-      if (svqb) ++*svqb;
+      st->svqb++;
       oracle_svqb(n, p, X, M);
-      continue;
+    } else {
+      for (int j = 0; j < p; ++j)
+        for (int64_t i = 0; i < n; ++i) X[i + (int64_t)j * n] *= Dv[j];
+      free(Dv);
+      right_solve_lower_transpose(n, p, X, L); /* X <- X D L^{-T} */
+      if (trim && !shifted && fro_off <= 0.5) { /* R17: ||L^{-T}||^2 <= 2, no re-check */
+        st->skipped_recheck++;
+        break;
+      }
     }
-    for (int j = 0; j < p; ++j)
-      for (int64_t i = 0; i < n; ++i) X[i + (int64_t)j * n] *= Dv[j];
-    free(Dv);
-    right_solve_lower_transpose(n, p, X, L); /* X <- X D L^{-T} */
+    oracle_gram(n, p, X, p, X, M); /* M = X^T X */
+    st->grams++;
   }
-  if (passes_max && passes > *passes_max) *passes_max = passes;
+  if (passes > st->cholqr_passes_max) st->cholqr_passes_max = passes;
+  st->passes = passes;
   free(M);
   free(L);
+  return passes;
+}
+
+/* Algorithm 3.  With trim (Sec. 3.2, the growth factor of ortho(X), reading R18): the
+ * projection X - Y C leaves a Y-component of about eps sqrt(q) ||x~_j|| per column, and
+ * ortho(X) amplifies it by g_j = (||x~_j|| / ||x_proj,j||) ||L^{-T}||, with ||x~_j||^2 =
+ * ||C_j||^2 + ||x_proj,j||^2 (Y orthonormal).  When eps sqrt(q) max_j g_j <= tau the
+ * overlap after the pass is below tau and the loop ends without forming Y^T X again. */
+static int ortho_against_impl(int64_t n, int p, double* X, int q, const double* Y, double tau, int cap,
+                              int cap2, int trim, oracle_ortho_stats* st) {
+  if (p <= 0) return 0;
+  double* C = (double*)malloc(sizeof(double) * (size_t)(q > 0 ? q : 1) * p);
+  double* d2 = (double*)malloc(sizeof(double) * (size_t)p);
+  int passes = 0, have_c = 0;
+  for (;;) {
+    if (q > 0) {
+      if (!have_c) {
+        oracle_gram(n, q, Y, p, X, C); /* C = Y^T X */
+        st->grams++;
+      }
+      block_minus_times(n, p, X, q, Y, C); /* X <- X - Y Y^T X */
+    }
+    oracle_ortho_stats in;
+    memset(&in, 0, sizeof in);
+    double l2 = 1.0;
+    ortho_impl(n, p, X, tau, cap, trim, &in, d2, &l2);
+    st->grams += in.grams, st->shifts += in.shifts, st->svqb += in.svqb, st->cap_hits += in.cap_hits;
+    st->skipped_recheck += in.skipped_recheck;
+    if (in.cholqr_passes_max > st->cholqr_passes_max) st->cholqr_passes_max = in.cholqr_passes_max;
+    ++passes;
+    if (q == 0) break;
+    if (trim && l2 < HUGE_VAL) {
+      double g2 = 0.0;
+      for (int j = 0; j < p; ++j) {
+        double c2 = 0.0;
+        for (int i = 0; i < q; ++i) c2 += C[i + (size_t)j * q] * C[i + (size_t)j * q];
+        const double gj = d2[j] > 0.0 ? (c2 + d2[j]) / d2[j] * l2 : HUGE_VAL;
+        if (!(gj <= g2)) g2 = gj;
+      }
+      if (EPS * sqrt((double)q) * sqrt(g2) <= tau) { /* R18: moderate growth, no test */
+        st->skipped_test++;
+        break;
+      }
+    }
+    oracle_gram(n, q, Y, p, X, C);
+    st->grams++;
+    have_c = 1;
+    if (max_abs((int64_t)q * p, C) <= tau) break;
+    if (passes >= cap2) {
+      st->cap_hits++;
+      break;
+    }
+  }
+  st->passes = passes;
+  free(C);
+  free(d2);
+  return passes;
+}
+
+int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, int* svqb,
+                 int* cap_hit, int* passes_max) {
+  oracle_ortho_stats st;
+  memset(&st, 0, sizeof st);
+  const int passes = ortho_impl(n, p, X, tau, cap, 0, &st, NULL, NULL);
+  if (shifts) *shifts += st.shifts;
+  if (svqb) *svqb += st.svqb;
+  if (cap_hit) *cap_hit += st.cap_hits;
+  if (passes_max && passes > *passes_max) *passes_max = passes;
   return passes;
 }
 
 int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, double tau,
                          int cap, int cap2, int* shifts, int* svqb, int* cap_hit,
                          int* cholqr_passes_max) {
-  if (p <= 0) return 0;
-  double* C = (double*)malloc(sizeof(double) * (size_t)(q > 0 ? q : 1) * p);
-  int passes = 0;
-  for (;;) {
-    if (q > 0) {
-      oracle_gram(n, q, Y, p, X, C); /* C = Y^T X */
-      block_minus_times(n, p, X, q, Y, C); /* X <- X - Y Y^T X */
-    }
-    oracle_ortho(n, p, X, tau, cap, shifts, svqb, cap_hit, cholqr_passes_max);
-    ++passes;
-    if (q == 0) break;
-    oracle_gram(n, q, Y, p, X, C);
-    if (max_abs((int64_t)q * p, C) <= tau) break;
-    if (passes >= cap2) {
-      if (cap_hit) ++*cap_hit;
-      break;
-    }
-  }
-  free(C);
+  oracle_ortho_stats st;
+  memset(&st, 0, sizeof st);
+  const int passes = ortho_against_impl(n, p, X, q, Y, tau, cap, cap2, 0, &st);
+  if (shifts) *shifts += st.shifts;
+  if (svqb) *svqb += st.svqb;
+  if (cap_hit) *cap_hit += st.cap_hits;
+  if (cholqr_passes_max && st.cholqr_passes_max > *cholqr_passes_max) *cholqr_passes_max = st.cholqr_passes_max;
   return passes;
+}
+
+int oracle_ortho_ex(int64_t n, int p, double* X, double tau, int cap, int trim, oracle_ortho_stats* st) {
+  memset(st, 0, sizeof *st);
+  return ortho_impl(n, p, X, tau, cap, trim, st, NULL, NULL);
+}
+
+int oracle_ortho_against_ex(int64_t n, int p, double* X, int q, const double* Y, double tau, int cap, int cap2,
+                            int trim, oracle_ortho_stats* st) {
+  memset(st, 0, sizeof *st);
+  return ortho_against_impl(n, p, X, q, Y, tau, cap, cap2, trim, st);
 }
 
 /* R16: drop the columns of W whose overlap with Y is above sqrt(tau) (and, with
@@ -488,6 +583,34 @@ static void finish_outputs(const oracle_matrix* A, int64_t n, int k, const doubl
   free(AXk);
 }
 
+/* Algorithm 2 / 3 on an n-row block with the run's options; statistics go to *loc.  The
+ * cost trims (R17, R18) apply to these n-row orthogonalisations only: the u_p one in
+ * R^s costs nothing worth saving. */
+static void add_stats(oracle_info* loc, const oracle_ortho_stats* st) {
+  loc->shifts += st->shifts;
+  loc->svqb += st->svqb;
+  loc->cap_hits += st->cap_hits;
+  loc->ortho_grams += st->grams;
+  loc->skipped_recheck += st->skipped_recheck;
+  loc->skipped_test += st->skipped_test;
+  if (st->cholqr_passes_max > loc->cholqr_passes_max) loc->cholqr_passes_max = st->cholqr_passes_max;
+}
+
+static void run_ortho(int64_t n, int p, double* X, double tau, int cap, int trim, oracle_info* loc) {
+  oracle_ortho_stats st;
+  oracle_ortho_ex(n, p, X, tau, cap, trim, &st);
+  add_stats(loc, &st);
+}
+
+static int run_ortho_against(int64_t n, int p, double* X, int q, const double* Y, double tau, int cap, int cap2,
+                             int trim, oracle_info* loc) {
+  oracle_ortho_stats st;
+  const int passes = oracle_ortho_against_ex(n, p, X, q, Y, tau, cap, cap2, trim, &st);
+  add_stats(loc, &st);
+  if (passes > loc->ortho_passes_max) loc->ortho_passes_max = passes;
+  return passes;
+}
+
 int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts* opt,
                   const double* X0, double* evals, double* evecs, double* resnorms,
                   oracle_info* info, oracle_history* hist) {
@@ -523,8 +646,7 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
 
   /* ---- Algorithm 1, initialisation ---- */
   memcpy(X, X0, sizeof(double) * n * m);
-  oracle_ortho(n, m, X, tau, cap, &loc.shifts, &loc.svqb, &loc.cap_hits,
-               &loc.cholqr_passes_max);                                   /* R2 */
+  run_ortho(n, m, X, tau, cap, opt->trim, &loc);                          /* R2 */
   oracle_apply(A, m, X, AX);                                              /* AX = A X */
   loc.spmm_columns += m;
   oracle_gram(n, m, X, m, AX, a);                                         /* a = X^T AX */
@@ -549,9 +671,7 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
   int w_cols = m_act; /* columns of W (R16) */
   {
     const int hits0 = loc.cap_hits;
-    int p2 = oracle_ortho_against(n, m_act, W, m, X, tau, cap, cap2, &loc.shifts, &loc.svqb,
-                                  &loc.cap_hits, &loc.cholqr_passes_max); /* W = ortho(W~; X) */
-    if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;
+    run_ortho_against(n, m_act, W, m, X, tau, cap, cap2, opt->trim, &loc); /* W = ortho(W~; X) */
     if (loc.cap_hits > hits0) w_cols = oracle_drop_unorthogonal_columns(n, m_act, W, m, X, tau, 1); /* R16 */
     loc.w_dropped += m_act - w_cols;
   }
@@ -624,9 +744,7 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     memcpy(Y + n * m, P, sizeof(double) * n * have_p);
     {
       const int hits0 = loc.cap_hits;
-      int p2 = oracle_ortho_against(n, m_act, W, m + have_p, Y, tau, cap, cap2, &loc.shifts,
-                                    &loc.svqb, &loc.cap_hits, &loc.cholqr_passes_max);
-      if (p2 > loc.ortho_passes_max) loc.ortho_passes_max = p2;           /* W = ortho(W~; (X, P)) */
+      run_ortho_against(n, m_act, W, m + have_p, Y, tau, cap, cap2, opt->trim, &loc); /* W = ortho(W~; (X, P)) */
       w_cols = m_act;
       if (loc.cap_hits > hits0)
         w_cols = oracle_drop_unorthogonal_columns(n, m_act, W, m + have_p, Y, tau, 1); /* R16 */

@@ -37,6 +37,7 @@ typedef struct {
   int ortho2_cap; /* cap on projection passes in ortho(X, Y)      (default 4) */
   double tol;     /* residual tolerance */
   double tau;     /* orthogonality threshold tau_ortho (Sec. 4: 1e-14) */
+  int trim;       /* 1: the cost trims of Sec. 3.2 in the n-row orthogonalisations (R17, R18) */
 } oracle_opts;
 
 typedef struct {
@@ -50,7 +51,19 @@ typedef struct {
   int spmm_columns;      /* columns multiplied by A, summed over the run */
   int w_dropped;         /* W columns dropped by R16, summed over the run */
   int p_dropped;         /* P columns dropped by R14 (x_j did not move) or R16, summed */
+  int ortho_grams;       /* n-row Gram matrices formed by the orthogonalisations of W and X0 */
+  int skipped_recheck;   /* Algorithm 2 re-check Grams skipped by the ||L^-T|| estimate (R17) */
+  int skipped_test;      /* Algorithm 3 test Grams skipped by the growth factor (R18) */
 } oracle_info;
+
+/* Statistics of one Algorithm 2 / 3 call. */
+typedef struct {
+  int passes;            /* Cholesky-QR passes (Algorithm 2) or projection passes (Algorithm 3) */
+  int grams;             /* n-row Gram matrices formed (X^T X and Y^T X) */
+  int shifts, svqb, cap_hits, cholqr_passes_max;
+  int skipped_recheck;   /* Algorithm 2 re-check Grams skipped (R17) */
+  int skipped_test;      /* Algorithm 3 test Grams skipped (R18) */
+} oracle_ortho_stats;
 
 /* Per-iteration history (optional; any pointer may be NULL).  Row t (t = 0 is the
  * initial Rayleigh-Ritz) holds the m Ritz values / residual norms and the active count. */
@@ -89,6 +102,17 @@ void oracle_svqb(int64_t n, int p, double* X, const double* M);
  * passes; *shifts / *svqb / *cap_hit accumulate (may be NULL). */
 int oracle_ortho(int64_t n, int p, double* X, double tau, int cap, int* shifts, int* svqb,
                  int* cap_hit, int* passes_max);
+
+/* Algorithm 2 with the optional cost trim of Sec. 3.2 (trim = 1, reading R17): the final
+ * re-check X^T X is skipped after an unshifted pass whose scaled overlap I + F has
+ * ||F||_F <= 1/2.  *st receives the call's statistics. */
+int oracle_ortho_ex(int64_t n, int p, double* X, double tau, int cap, int trim, oracle_ortho_stats* st);
+
+/* Algorithm 3 with the optional cost trim of Sec. 3.2 (trim = 1, reading R18): the test
+ * Y^T X is skipped when eps sqrt(q) times the growth factor of the pass is <= tau (and the
+ * Algorithm 2 calls inside use R17). */
+int oracle_ortho_against_ex(int64_t n, int p, double* X, int q, const double* Y, double tau, int cap, int cap2,
+                            int trim, oracle_ortho_stats* st);
 
 /* Algorithm 3 in place: orthonormalise X (n x p) against orthonormal Y (n x q).
  * Returns the number of projection passes. */

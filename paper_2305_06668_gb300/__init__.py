@@ -41,7 +41,7 @@ class _Options(C.Structure):
     _fields_ = [("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
                 ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
-                ("mixed_switch", C.c_double), ("autotune", C.c_int)]
+                ("mixed_switch", C.c_double), ("autotune", C.c_int), ("ortho_trim", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -54,7 +54,8 @@ class _Info(C.Structure):
                 ("spmm_columns_fp64", C.c_int64), ("update_fp64_seconds", C.c_double),
                 ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64),
                 ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int), ("w_dropped", C.c_int),
-                ("p_dropped", C.c_int)]
+                ("p_dropped", C.c_int), ("ortho_grams", C.c_int), ("skipped_recheck", C.c_int),
+                ("skipped_test", C.c_int)]
 
 
 def library_path() -> pathlib.Path:
@@ -73,7 +74,8 @@ def lib():
                      "lobpcg_ortho_against_f64", "lobpcg_gram_f64_noalloc", "lobpcg_mlp_forward",
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
-                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32"):
+                     "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32",
+                     "lobpcg_probe_fma_rate"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -141,7 +143,7 @@ class Solver:
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
                  mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
-                 stream=None):
+                 ortho_trim: bool = True, stream=None):
         torch = _torch()
         L = lib()
         self._keep = [diag, row_ptr, col_idx, val, dense]
@@ -167,6 +169,7 @@ class Solver:
         o.profile = 1 if profile else 0
         o.mixed_switch = mixed_switch
         o.autotune = 1 if autotune else 0
+        o.ortho_trim = 1 if ortho_trim else 0
         w = None
         if mlp_weights is not None:
             w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
@@ -310,6 +313,13 @@ def update_f32(V, U, q=None, alpha=1.0, AV=None, base=None, X=None, AX=None, lam
     if resnorm:
         return X, AX, np.array(rn[:])
     return X, AX
+
+
+def probe_fma_rate(fp64: bool = True, stream=None) -> float:
+    """Measured peak FMA rate of the current GPU in TFLOP/s (FP64 or FP32 pipes)."""
+    out = C.c_double(0.0)
+    _check(lib().lobpcg_probe_fma_rate(C.c_int(1 if fp64 else 0), C.byref(out), _stream(stream)))
+    return out.value
 
 
 def gram_noalloc(X, Y, out=None, stream=None):

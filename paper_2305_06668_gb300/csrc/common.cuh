@@ -186,8 +186,11 @@ void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U
 //  ctl[0] <- 1 if max|M - I| <= tau (already orthonormal), else 0 and Linv <- L^{-T}
 //  of chol(M + shift) (upper triangular, column-major p x p).  ctl[1] += shifted
 //  attempts, ctl[2] += 1 if SVQB had to be used (then Linv holds the SVQB transform).
+//  ctl[6] <- 1 if the pass was unshifted with ||D M D - I||_F <= 1/2 (reading R17);
+//  with C (q x p, first call of an Algorithm 3 pass) ctl[7] <- 1 if the pass's growth
+//  factor squared is <= growth2 (reading R18).
 void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl,
-                         cudaStream_t st);
+                         cudaStream_t st, const double* C = nullptr, int q = 0, double growth2 = 0.0);
 // max |C - I| over a p x p matrix -> *out (device double)
 void launch_maxabs_minus_identity(int p, const double* C, double* out, cudaStream_t st);
 // max |C| over a p x q matrix -> *out (device double)

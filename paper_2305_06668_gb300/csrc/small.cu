@@ -470,9 +470,15 @@ __device__ void svqb_cta(int p, const double* M, int ldm, double* B, double* Z, 
   __syncthreads();
 }
 
+// ctl[6] <- 1 when this pass factored an unshifted scaled overlap I + F with ||F||_F <= 1/2
+// (||L^{-T}||_2^2 <= 2: the re-check Gram of Algorithm 2 can be skipped, reading R17).
+// With C (q x p, column-major, the projection coefficients of this Algorithm 3 pass; only
+// on the first call of the pass): ctl[7] <- 1 when the growth factor satisfies
+// max_j (||C_j||^2 + M_jj) / M_jj * ||L^{-T}||^2 <= growth2 (reading R18).
 __global__ void __launch_bounds__(kSmallThreads) cholqr_small_kernel(int p, const double* __restrict__ Min,
                                                                      double tau, double* __restrict__ Tout,
-                                                                     int* ctl) {
+                                                                     int* ctl, const double* __restrict__ C,
+                                                                     int q, double growth2) {
   extern __shared__ double sm[];
   __shared__ double red[32];
   __shared__ double rot[4 * (kMaxS / 2 + 1)];
@@ -494,17 +500,39 @@ __global__ void __launch_bounds__(kSmallThreads) cholqr_small_kernel(int p, cons
   }
   if (threadIdx.x == 0) shifts = 0;
   dev = block_max(dev, red);
+  // growth factor of the Algorithm 3 pass (R18): amplification ||x~_j|| / ||x_proj,j|| of
+  // column j times the bound on ||L^{-T}||; here the squared column term, the bound below
+  double g2 = 0.0;
+  if (C) {
+    for (int j = threadIdx.x; j < p; j += blockDim.x) {
+      double c2 = 0.0;
+      for (int i = 0; i < q; ++i) c2 += C[i + j * q] * C[i + j * q];
+      const double mjj = M[j + j * ld];
+      const double gj = mjj > 0.0 ? (c2 + mjj) / mjj : INFINITY;
+      g2 = (gj <= g2) ? g2 : gj;
+    }
+    g2 = block_max(g2, red);
+  }
   if (dev <= tau) {
-    if (threadIdx.x == 0) ctl[0] = 1;
+    if (threadIdx.x == 0) {
+      ctl[0] = 1;
+      ctl[6] = 0;
+      if (C) ctl[7] = g2 <= growth2 ? 1 : 0;
+    }
     return;
   }
   // scaled Cholesky-QR: factor D M D with D = diag(M)^{-1/2}, transform T = D L^{-T}
   for (int i = threadIdx.x; i < p; i += blockDim.x) theta[i] = M[i + i * ld] > 0.0 ? rsqrt(M[i + i * ld]) : 1.0;
   __syncthreads();
+  double fro = 0.0;  // ||F||_F of the scaled overlap D M D = I + F
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
     const int i = e % p, j = e / p;
-    Z[i + j * ld] = theta[i] * M[i + j * ld] * theta[j];
+    const double z = theta[i] * M[i + j * ld] * theta[j];
+    Z[i + j * ld] = z;
+    const double f = z - (i == j ? 1.0 : 0.0);
+    fro += f * f;
   }
+  fro = sqrt(block_sum(fro, red));
   __syncthreads();
   const int fail = shifted_chol_cta(p, Z, ld, L, ld, &flag, &shifts, red);
   if (!fail) {
@@ -519,9 +547,15 @@ __global__ void __launch_bounds__(kSmallThreads) cholqr_small_kernel(int p, cons
   }
   for (int e = threadIdx.x; e < p * p; e += blockDim.x) Tout[e] = T[(e % p) + (e / p) * ld];
   if (threadIdx.x == 0) {
+    const bool clean = !fail && shifts == 0;
     ctl[0] = 0;
     ctl[1] += shifts;
     ctl[2] += fail ? 1 : 0;
+    ctl[6] = clean && fro <= 0.5 ? 1 : 0;
+    if (C) {
+      const double l2 = clean && fro < 1.0 ? 1.0 / (1.0 - fro) : INFINITY;
+      ctl[7] = g2 * l2 <= growth2 ? 1 : 0;
+    }
   }
 }
 
@@ -767,7 +801,8 @@ void launch_syev(int s, const double* a, bool upper_only, double* lam, double* U
   LB_LAUNCH_CHECK();
 }
 
-void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl, cudaStream_t st) {
+void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* ctl, cudaStream_t st,
+                         const double* C, int q, double growth2) {
   if (p <= 0) return;
   if (p > kMaxCholP) throw std::invalid_argument("cholqr: p > 64");
   const size_t smem = (size_t)4 * p * (p + 1) * sizeof(double);
@@ -777,7 +812,7 @@ void launch_cholqr_small(int p, const double* M, double tau, double* Linv, int* 
     return true;
   }();
   (void)attr;
-  cholqr_small_kernel<<<1, kSmallThreads, smem, st>>>(p, M, tau, Linv, ctl);
+  cholqr_small_kernel<<<1, kSmallThreads, smem, st>>>(p, M, tau, Linv, ctl, C, q, growth2);
   LB_LAUNCH_CHECK();
 }
 

@@ -85,6 +85,7 @@ struct Stats {
   int precond_fallback = 0;
   int w_dropped = 0;
   int p_dropped = 0;
+  int ortho_grams = 0, skipped_recheck = 0, skipped_test = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -417,19 +418,33 @@ void right_multiply(lobpcg_ctx& c, T* W, int ld, int p, const double* Tm) {
   update<T>(c, job, Tm, p, p, 1.0, nullptr, nullptr);
 }
 
-// Algorithm 2: W (n x p) <- ortho(W).  Host-driven loop, one flag read per pass.
+// Algorithm 2: W (n x p) <- ortho(W).  Host-driven loop, one flag read per pass.  With
+// opt.ortho_trim the re-check Gram is skipped after an unshifted pass whose scaled overlap
+// I + F had ||F||_F <= 1/2 (reading R17, the ||L^{-T}|| estimate of Sec. 3.2).  Cg (q x p,
+// the coefficients of the projection just applied by Algorithm 3) asks the first
+// factorisation for the pass's growth factor test (reading R18); *growth_ok receives it.
 template <class T>
-int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap) {
+int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap, const double* Cg = nullptr, int q = 0,
+          bool* growth_ok = nullptr) {
+  if (growth_ok) *growth_ok = false;
   if (p <= 0) return 0;
+  const bool trim = c.opt.ortho_trim != 0;
+  // eps sqrt(q) g <= tau with the unit of the block's arithmetic (reading R18)
+  const double eps = sizeof(T) == 4 ? 1.1920928955078125e-07 : 2.220446049250313e-16;
+  const double g_max = q > 0 ? tau / (eps * std::sqrt((double)q)) : 0.0;
   int passes = 0;
-  LB_CUDA(cudaMemsetAsync(c.ictl, 0, 4 * sizeof(int), c.st));
-  for (;;) {
+  LB_CUDA(cudaMemsetAsync(c.ictl, 0, 8 * sizeof(int), c.st));
+  const int* h = reinterpret_cast<const int*>(c.host);
+  for (int call = 0;; ++call) {
     const Cols<T> w = cols1<T>(W, ld, p);
     gram<T>(c, w, w, false, c.G);                       // M = W^T W
-    launch_cholqr_small(p, c.G, tau, c.Tm, c.ictl, c.st);  // test ||M - I||, factor
-    LB_CUDA(cudaMemcpyAsync(c.host, c.ictl, 4 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    c.stats.ortho_grams++;
+    const bool want_growth = trim && call == 0 && Cg && growth_ok;
+    launch_cholqr_small(p, c.G, tau, c.Tm, c.ictl, c.st, want_growth ? Cg : nullptr, q,
+                        g_max * g_max);                 // test ||M - I||, factor
+    LB_CUDA(cudaMemcpyAsync(c.host, c.ictl, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
     c.sync();
-    const int* h = reinterpret_cast<const int*>(c.host);
+    if (want_growth) *growth_ok = h[7] != 0;
     if (h[0]) break;
     if (passes >= cap) {
       c.stats.cap_hits++;
@@ -437,8 +452,11 @@ int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap) {
     }
     ++passes;
     right_multiply<T>(c, W, ld, p, c.Tm);               // W <- W L^{-T}
+    if (trim && h[6]) {                                 // R17: ||L^{-T}||^2 <= 2, no re-check
+      c.stats.skipped_recheck++;
+      break;
+    }
   }
-  const int* h = reinterpret_cast<const int*>(c.host);
   c.stats.shifts += h[1];
   c.stats.svqb += h[2];
   c.stats.cholqr_passes_max = std::max(c.stats.cholqr_passes_max, passes);
@@ -461,9 +479,13 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
   double last = 0.0;
   bool c_ready = false;  // C = Y^T W of the current W is already in c.C (the previous pass's test)
   c.prof.mark(PH_ORTHO);
+  bool c_current = true;  // c.C = Y^T W of the final W (false after a growth-factor exit)
   for (;;) {
     if (q > 0) {
-      if (!c_ready) gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);  // C = Y^T W
+      if (!c_ready) {
+        gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);  // C = Y^T W
+        c.stats.ortho_grams++;
+      }
       UpdateJob<T> job{};
       job.in[0] = Y;
       job.out[0] = W;
@@ -473,10 +495,17 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
       job.nprod = 1;
       update<T>(c, job, c.C, q, p, -1.0, nullptr, nullptr);  // W -= Y C
     }
-    ortho<T>(c, W, ld, p, tau, cap);
+    bool growth_ok = false;
+    ortho<T>(c, W, ld, p, tau, cap, q > 0 ? c.C : nullptr, q, &growth_ok);
     ++passes;
     if (q == 0) break;
+    if (growth_ok) {  // R18: moderate growth factor, the overlap with Y is below tau
+      c.stats.skipped_test++;
+      c_current = false;
+      break;
+    }
     gram<T>(c, Y, cols1<T>(W, ld, p), false, c.C);
+    c.stats.ortho_grams++;
     launch_maxabs(q * p, c.C, c.scal, c.st);
     LB_CUDA(cudaMemcpyAsync(c.host, c.scal, sizeof(double), cudaMemcpyDeviceToHost, c.st));
     c.sync();
@@ -491,6 +520,7 @@ int ortho_against(lobpcg_ctx& c, T* W, int ld, int p, const Cols<T>& Y, double t
   if (kept && c.stats.cap_hits > hits0) {
     // R16: c.C holds Y^T W of the final W (the last pass's test); the norms come from W^T W
     const Cols<T> w = cols1<T>(W, ld, p);
+    if (q > 0 && !c_current) gram<T>(c, Y, w, false, c.C);
     gram<T>(c, w, w, false, c.G);
     std::vector<double> Ch((size_t)q * p), Mh((size_t)p * p);
     if (q > 0) LB_CUDA(cudaMemcpyAsync(Ch.data(), c.C, Ch.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
@@ -778,6 +808,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->seed = 0;
   opt->mlp_weights = nullptr;
   opt->autotune = 0;
+  opt->ortho_trim = 1;
   return LOBPCG_OK;
 }
 
@@ -999,6 +1030,9 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->spmm_variant_fp64 = c->var64;
       info->w_dropped = c->stats.w_dropped;
       info->p_dropped = c->stats.p_dropped;
+      info->ortho_grams = c->stats.ortho_grams;
+      info->skipped_recheck = c->stats.skipped_recheck;
+      info->skipped_test = c->stats.skipped_test;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))

@@ -370,3 +370,17 @@ def test_update_f32_staged_and_general_layouts_agree():
         out[ld] = (X.cpu().numpy(), AX.cpu().numpy(), np.asarray(rn))
     assert np.array_equal(out[24][0], out[23][0]) and np.array_equal(out[24][1], out[23][1])
     assert np.all(np.abs(out[24][2] - out[23][2]) <= 1e-6 * out[24][2])
+
+
+def test_fma_rate_probe_is_plausible():
+    """The FMA-rate probe (the denominator of the FMA-bound rooflines) returns rates inside
+    what the part can do: FP64 near 2 FMA per clock per SM, FP32 near 128."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    props = torch.cuda.get_device_properties(0)
+    sms = props.multi_processor_count
+    f64 = lb.probe_fma_rate(fp64=True)
+    f32 = lb.probe_fma_rate(fp64=False)
+    ghz_max = 2.2  # above the part's 2.07 GHz boost clock
+    assert 0.0 < f64 <= sms * 4 * ghz_max * 1e-3 * 1.05
+    assert f64 * 8 < f32 <= sms * 256 * ghz_max * 1e-3 * 1.05

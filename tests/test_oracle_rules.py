@@ -106,7 +106,9 @@ def _exact_pair_problem(n=20, seed=37):
     """Diagonal A = diag(1..n); x_1 = e_0 + noise (noise zero at row 1) and x_2 = e_1 exactly.
     x_2 is an exact eigenvector behind an unconverged x_1, so it stays active; every
     coupling with it is exactly zero, its Jacobi column stays a unit vector (u~_p = 0) and
-    its residual, hence its W~ column, is exactly zero."""
+    its residual, hence its W~ column, is exactly zero.  Solved without a preconditioner:
+    for a diagonal A the diagonal one is exact, T r_1 is parallel to x_1 and its projection
+    is rounding noise, a second degeneracy that would hide this one."""
     d = np.arange(1.0, n + 1)
     x1 = np.zeros(n)
     x1[0] = 1.0
@@ -118,7 +120,7 @@ def _exact_pair_problem(n=20, seed=37):
 
 def test_exact_active_pair_drops_its_p_and_w_columns():
     A, d, X0 = _exact_pair_problem()
-    r = oracle.lobpcg(A, d, 2, X0, tol=1e-10, maxiter=200)
+    r = oracle.lobpcg(A, d, 2, X0, tol=1e-10, maxiter=200, precond=0)
     assert r.status == 0
     assert np.max(np.abs(r.evals - [1.0, 2.0])) <= 1e-14
     assert np.all(np.isfinite(r.resnorms)) and np.max(r.resnorms) <= 1e-10
@@ -142,3 +144,71 @@ def test_cfg1_run_never_drops():
     # the basis has its full width at every step: W = m_act columns, P = m_act of the previous step
     assert np.all(r.hist_wcols[1:] == r.hist_mact[:-1])
     assert r.hist_pcols[1] == 0 and np.all(r.hist_pcols[2:] == r.hist_mact[1:-1])
+
+
+# ------------------------------------------------------------- R17, R18 (Sec. 3.2 trims)
+
+def test_recheck_skip_only_after_a_well_conditioned_pass():
+    """R17: the re-check Gram of Algorithm 2 is skipped only after an unshifted pass with
+    ||F||_F <= 1/2 (F = scaled overlap - I), where ||L^-T||^2 <= 2 and the new vectors are
+    orthonormal to the Gram's rounding.  A nearly orthonormal block (||F||_F ~ 0.2) needs
+    one pass and no re-check; an ill-conditioned one (cond ~ 1e5) gets its re-check after
+    the first pass and skips it after the second.  The output equals the printed
+    algorithm's bit for bit (the skipped test would have passed) and is orthonormal to tau
+    checked in numpy."""
+    n, p = 600, 6
+    good = synth.gaussian_block(n, p, seed=40)
+    bad = good.copy()
+    bad[:, 3] = bad[:, 1] + 1e-5 * bad[:, 3]  # nearly dependent columns
+    for X, grams_trim, grams_plain in ((good, 1, 2), (bad, 2, 3)):
+        Q0, s0 = oracle.ortho(X, trim=False)
+        Q1, s1 = oracle.ortho(X, trim=True)
+        assert np.array_equal(Q0, Q1) and s0["passes"] == s1["passes"]
+        assert s1["grams"] == grams_trim and s0["grams"] == grams_plain
+        assert s1["skipped_recheck"] == 1 and s0["skipped_recheck"] == 0
+        assert np.max(np.abs(Q1.T @ Q1 - np.eye(p))) <= 1e-14
+
+
+def test_growth_factor_exit_only_when_little_was_projected_out():
+    """R18: Algorithm 3 skips its test Gram Y^T X when eps sqrt(q) g <= tau, g the growth
+    factor ||x~_j|| / ||x_proj,j|| * ||L^-T|| of the pass.  A block with a small component
+    in span(Y) has g ~ 1: one pass, no test Gram, same output as the printed algorithm and
+    orthogonal to Y to tau (numpy).  A block almost inside span(Y) (g ~ 1e6) keeps the
+    test after its first pass and takes a second one, whose growth is ~1 again (its test
+    is skipped)."""
+    n, q, p = 600, 8, 5
+    Y = _orthonormal(n, q, seed=41)
+    Xs = synth.gaussian_block(n, p, seed=42)
+    near = Y @ synth.gaussian_block(q, p, seed=43) + 1e-6 * Xs
+    for Xt, passes, skipped in ((Xs, 1, 1), (near, 2, 1)):
+        Q0, s0 = oracle.ortho_against(Xt, Y, trim=False)
+        Q1, s1 = oracle.ortho_against(Xt, Y, trim=True)
+        assert s1["passes"] == passes and s1["skipped_test"] == skipped
+        assert np.array_equal(Q0, Q1) and s0["passes"] == passes
+        assert s0["grams"] - s1["grams"] == skipped + s1["skipped_recheck"]
+        assert np.max(np.abs(Y.T @ Q1)) <= 1e-14
+        assert np.max(np.abs(Q1.T @ Q1 - np.eye(p))) <= 1e-14
+
+
+@pytest.mark.parametrize("case", ["cfg1", "ci", "dense"])
+def test_trimmed_lobpcg_is_the_printed_one_with_fewer_grams(case):
+    """On these runs every skipped Gram's test would have passed, so the trimmed method
+    reproduces the printed Algorithms 2-3 bit for bit with 15-30% fewer orthogonalisation
+    Grams (the paper's claim of <= 4 Cholesky-QR passes and ~2 ortho(X, Y) passes holds)."""
+    if case == "cfg1":
+        a = synth.sparse_cfg1()
+        A, d, k, extra, x0 = a, a.diag, 4, 0, synth.diag_guess(a.diag, 4, seed=0)
+    elif case == "ci":
+        a = synth.sparse_ci(n=20_011, seed=2105)
+        A, d, k, extra, x0 = a, a.diag, 6, 2, synth.diag_guess(a.diag, 8, seed=2105, noise=0.0)
+    else:
+        A, d = synth.dense_casscf(n=1024, seed=2, rank=64)
+        k, extra, x0 = 4, 0, synth.diag_guess(d, 4, seed=2)
+    r0 = oracle.lobpcg(A, d, k, x0, extra=extra, tol=1e-8, maxiter=3000, trim=False)
+    r1 = oracle.lobpcg(A, d, k, x0, extra=extra, tol=1e-8, maxiter=3000, trim=True)
+    assert r0.status == 0 and r1.status == 0
+    assert np.array_equal(r0.evals, r1.evals) and np.array_equal(r0.evecs, r1.evecs)
+    saved = r1.info["skipped_recheck"] + r1.info["skipped_test"]
+    assert r0.info["ortho_grams"] - r1.info["ortho_grams"] == saved
+    assert 0.15 * r0.info["ortho_grams"] <= saved
+    assert r1.info["cholqr_passes_max"] <= 4 and r1.info["ortho_passes_max"] <= 3
