@@ -112,7 +112,15 @@ typedef struct {
                                  (bounded from the scaled overlap I + F by 1 / (1 - ||F||_F));
                                  Algorithm 3 skips its test Gram when eps sqrt(q) times the growth
                                  factor of ortho (column amplification times that bound) is <=
-                                 tau.  0: the printed Algorithms 2 and 3 */
+                                 tau.  Applies to the FP64 phases (the FP32 phase's Grams are not
+                                 accurate to a few eps).  0: the printed Algorithms 2 and 3 */
+  int df_products;            /* arithmetic of the FP64 Grams and block updates (not in the paper).
+                                 FP64 data and results either way; double-float forms each product
+                                 and sum from pairs of floats with error-free transformations on
+                                 the FP32 pipes (about 2^-48 per product, chunk sums in FP64).
+                                 0 (default): double-float in the FP64 refinement of the MIXED
+                                 form, FP64 fused multiply-adds in the FP64 form; 1: double-float
+                                 in every FP64 phase; -1: FP64 fused multiply-adds everywhere */
 } lobpcg_options;
 
 typedef struct {
@@ -146,6 +154,7 @@ typedef struct {
   int ortho_grams;              /* n-row Gram matrices formed by Algorithms 2 and 3 */
   int skipped_recheck;          /* Algorithm 2 re-check Grams skipped (ortho_trim) */
   int skipped_test;             /* Algorithm 3 test Grams skipped (ortho_trim) */
+  int df_products;              /* 1 if the FP64 Grams and updates ran in double-float arithmetic */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
@@ -210,6 +219,15 @@ LOBPCG_API lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, 
                                   const double* val, int p, const double* X, int ldx, double* Y,
                                   int ldy, lobpcg_stream stream);
 
+/* Y = A X for CSR A (nnz entries) like lobpcg_spmm_csr_f64, formed in double-float
+ * arithmetic on the FP32 pipes (the FP64 refinement's product, see
+ * lobpcg_options.df_products): values and X split into float pairs, compensated row sums,
+ * FP64 result.  X, Y: 16-byte aligned, even row strides; p <= 32.  Allocates the split
+ * copies on every call.  Not in the paper; the operation is Algorithm 1's A W. */
+LOBPCG_API lobpcg_status lobpcg_spmm_csr_f64_df(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                                const double* val, int64_t nnz, int p, const double* X, int ldx,
+                                                double* Y, int ldy, lobpcg_stream stream);
+
 /* Y = A X in FP32 with A's values rounded to FP32: the product of the mixed form
  * (Algorithm 1, "AW = A W", with FP32 blocks).  X, Y: n x p float, row-major, 16-byte
  * aligned with ldx, ldy multiples of 4; p <= 32.  band = -1 picks the half-width b that
@@ -232,6 +250,22 @@ LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64
  * X: n x p (ldx), Y: n x q (ldy), p, q <= 96.  C: device, column-major p x q. */
 LOBPCG_API lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int ldx, int q, const double* Y,
                               int ldy, double* C, lobpcg_stream stream);
+
+/* C = X^T Y like lobpcg_gram_f64, formed in double-float arithmetic on the FP32 pipes (the
+ * arithmetic of the FP64 refinement, see lobpcg_options.df_products): each FP64 element is
+ * split into two floats, products and sums are error-compensated, sums of ~128 rows are
+ * added in FP64.  X, Y: 16-byte aligned, one even row stride (ldx == ldy).  Not in the
+ * paper; the operation is Algorithm 1's Gram. */
+LOBPCG_API lobpcg_status lobpcg_gram_f64_df(int64_t n, int p, const double* X, int ldx, int q, const double* Y,
+                                            int ldy, double* C, lobpcg_stream stream);
+
+/* The FP64 block update X = base + alpha [V_g] U (and AX, residual norms) in double-float
+ * arithmetic; arguments as lobpcg_update_f32 with FP64 blocks (V_g, AV_g, base, X, AX:
+ * double, row stride ld / ld_base / ld_out in doubles). */
+LOBPCG_API lobpcg_status lobpcg_update_f64_df(int64_t n, int nseg, const double* const* V, const double* const* AV,
+                                              const int* w, int ld, const double* U, int q, double alpha,
+                                              const double* base, int ld_base, double* X, double* AX, int ld_out,
+                                              const double* lam, double* resnorm, lobpcg_stream stream);
 
 /* The block update of Algorithm 1 for FP32 blocks: X = base + alpha [V_0 .. V_{nseg-1}] U
  * and, with AV, AX = alpha [AV_0 ..] U (the basis and residual update X <- V u_x, AX <- AV u_x,

@@ -227,6 +227,34 @@ def drop_unorthogonal_columns(W: np.ndarray, Y: np.ndarray | None, tau: float = 
     return W[:, :kept]
 
 
+def lobpcg_gen(A, B, dA, dB, k: int, X0: np.ndarray, tol: float = 1e-8, extra: int = 0, maxiter: int = 1000,
+               tol_kind: int = 0, precond: int = 1, tau: float = 1e-14, ortho_cap: int = 6,
+               ortho2_cap: int = 4, hist_cap: int | None = None, trim: bool = True) -> Result:
+    """Algorithm 1 for A x = lambda B x (Sec. 3.3); A, B CSR (synth.CSR) or dense ndarrays."""
+    opA, opB = _operator(A), _operator(B)
+    n = opA.n
+    m = k + extra
+    X0 = _f64(X0)
+    assert X0.shape == (n, m), (X0.shape, n, m)
+    da = None if dA is None else np.ascontiguousarray(dA, dtype=np.float64)
+    db = None if dB is None else np.ascontiguousarray(dB, dtype=np.float64)
+    opts = _Opts(k, extra, maxiter, tol_kind, precond, ortho_cap, ortho2_cap, tol, tau, 1 if trim else 0)
+    evals = np.zeros(k)
+    evecs = np.zeros((n, k), order="F")
+    res = np.zeros(k)
+    info = _Info()
+    cap = (maxiter + 1) if hist_cap is None else hist_cap
+    hl, hr = np.zeros((cap, m)), np.zeros((cap, m))
+    hm, hw, hp = (np.zeros(cap, dtype=np.int32) for _ in range(3))
+    hist = _Hist(cap, _p(hl), _p(hr), _p(hm), 0, _p(hw), _p(hp))
+    lib().oracle_lobpcg_gen.restype = C.c_int
+    st = lib().oracle_lobpcg_gen(C.byref(opA.s), C.byref(opB.s), _p(da), _p(db), C.byref(opts), _p(X0),
+                                 _p(evals), _p(evecs), _p(res), C.byref(info), C.byref(hist))
+    info_d = {f: getattr(info, f) for f, _ in _Info._fields_}
+    r = hist.rows
+    return Result(st, evals, evecs, res, info_d, hl[:r], hr[:r], hm[:r], hw[:r], hp[:r])
+
+
 def threads() -> int:
     return lib().oracle_threads()
 

@@ -764,3 +764,323 @@ done:
   free(AV), free(a), free(U), free(lam_all), free(lam), free(up), free(nrm), free(conv);
   return status;
 }
+
+/* ================================================ generalised problem A x = lambda B x (Sec. 3.3)
+ *
+ * B symmetric positive definite.  The basis V = (X, W, P) is kept B-orthonormal, so the
+ * Rayleigh-Ritz problem stays the standard one a = V^T A V; B V is carried along like A V
+ * and updated by the same coefficients.  Following Sec. 3.3:
+ *   - W^ = ortho(W~, (B X, B P)): Algorithm 3 against an orthonormal basis Q of
+ *     span(B X, B P) (reading R19: the printed ortho(X, Y) needs orthonormal Y, so Q is
+ *     formed from (B X, B P) with Algorithm 2).  W^ is then B-orthogonal to X and P and
+ *     orthonormal in the Euclidean product, hence well conditioned in the B product.
+ *   - W = W^ L^{-T} with L L^T = W^T B W^ (Cholesky-QR in the B product, repeated while
+ *     ||W^T B W - I|| > tau as in Algorithm 2), and B W = (B W^) L^{-T} re-using the one
+ *     application of B to W^.
+ * Residuals are A x - lambda B x, the diagonal preconditioner is
+ * (diag(A) - theta diag(B))^{-1} (guarded as in R6), and x_j is returned with x^T B x = 1.
+ * X0 is B-orthonormalised the same way (reading R20).  Without B (B = I) every step reduces
+ * to Algorithm 1 exactly. */
+
+/* T (p x p) of one Cholesky-QR pass on the overlap M (R15 scaling, R4 shift, SVQB when
+ * the shift fails): X <- X T.  Counts go to loc. */
+static void cholqr_transform(int p, const double* M, double* T, oracle_info* loc) {
+  double* Dv = (double*)malloc(sizeof(double) * (size_t)p);
+  double* Ms = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* L = (double*)malloc(sizeof(double) * (size_t)p * p);
+  for (int i = 0; i < p; ++i) Dv[i] = M[i + i * p] > 0.0 ? 1.0 / sqrt(M[i + i * p]) : 1.0;
+  for (int j = 0; j < p; ++j)
+    for (int i = 0; i < p; ++i) Ms[i + j * p] = Dv[i] * M[i + j * p] * Dv[j];
+  memcpy(L, Ms, sizeof(double) * (size_t)p * p);
+  int fail = oracle_cholesky(p, L);
+  if (fail) {
+    double tr = 0.0;
+    for (int i = 0; i < p; ++i) tr += Ms[i + i * p];
+    double sigma = 100.0 * EPS * tr;
+    for (int t = 0; t < 8 && fail; ++t, sigma *= 10.0) {
+      memcpy(L, Ms, sizeof(double) * (size_t)p * p);
+      for (int i = 0; i < p; ++i) L[i + i * p] += sigma;
+      loc->shifts++;
+      fail = oracle_cholesky(p, L);
+    }
+  }
+  if (!fail) {
+    /* T = D L^{-T}: column j of L^{-T} is row j of L^{-1} (forward substitution) */
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i) T[i + j * p] = 0.0;
+    for (int c = 0; c < p; ++c) { /* column c of L^{-1} */
+      for (int i = 0; i < p; ++i) {
+        double s = i == c ? 1.0 : 0.0;
+        for (int l = 0; l < i; ++l) s -= L[i + l * p] * T[c + l * p];
+        T[c + i * p] = i < c ? 0.0 : s / L[i + i * p]; /* T(c, i) = (L^{-1})(i, c) */
+      }
+    }
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < p; ++i) T[i + j * p] *= Dv[i];
+  } else {
+    /* SVQB: D M D = Z Theta Z^T, T = D Z Theta^{-1/2} (Theta floored at eps max) */
+    double* Z = (double*)malloc(sizeof(double) * (size_t)p * p);
+    double* th = (double*)malloc(sizeof(double) * (size_t)p);
+    loc->svqb++;
+    oracle_jacobi_eig(p, Ms, th, Z);
+    double tmax = 0.0;
+    for (int i = 0; i < p; ++i) tmax = fmax(tmax, th[i]);
+    for (int j = 0; j < p; ++j) {
+      const double t = fmax(th[j], EPS * tmax);
+      for (int i = 0; i < p; ++i) T[i + j * p] = Dv[i] * Z[i + j * p] / sqrt(t);
+    }
+    free(Z), free(th);
+  }
+  free(Dv), free(Ms), free(L);
+}
+
+/* X <- X T and, when Y != NULL, Y <- Y T (same T): the re-use of B applications. */
+static void apply_transform(int64_t n, int p, double* X, double* Y, const double* T) {
+  double* tmp = (double*)malloc(sizeof(double) * (size_t)n * p);
+  memcpy(tmp, X, sizeof(double) * (size_t)n * p);
+  block_times_small(n, p, tmp, p, T, X);
+  if (Y) {
+    memcpy(tmp, Y, sizeof(double) * (size_t)n * p);
+    block_times_small(n, p, tmp, p, T, Y);
+  }
+  free(tmp);
+}
+
+/* Algorithm 2 in the B product with re-use: M = X^T (B X), stop when ||M - I|| <= tau,
+ * else X <- X T and B X <- (B X) T.  Returns the passes; a cap hit is counted. */
+static int b_ortho(int64_t n, int p, double* X, double* BX, double tau, int cap, oracle_info* loc) {
+  if (p <= 0) return 0;
+  double* M = (double*)malloc(sizeof(double) * (size_t)p * p);
+  double* T = (double*)malloc(sizeof(double) * (size_t)p * p);
+  int passes = 0;
+  for (;;) {
+    oracle_gram(n, p, X, p, BX, M);
+    for (int j = 0; j < p; ++j)
+      for (int i = 0; i < j; ++i) M[i + j * p] = M[j + i * p] = 0.5 * (M[i + j * p] + M[j + i * p]);
+    if (max_abs_minus_identity(p, M) <= tau) break;
+    if (passes >= cap) {
+      loc->cap_hits++;
+      break;
+    }
+    ++passes;
+    cholqr_transform(p, M, T, loc);
+    apply_transform(n, p, X, BX, T);
+  }
+  if (passes > loc->cholqr_passes_max) loc->cholqr_passes_max = passes;
+  free(M), free(T);
+  return passes;
+}
+
+/* R16 in the generalised form: keep the columns of W (and B W) whose overlap with the
+ * orthonormal Q is <= sqrt(tau) and whose B-norm is 1 to sqrt(tau); pack to the front. */
+static int drop_gen(int64_t n, int p, double* W, double* BW, int q, const double* Q, double tau) {
+  double* Cm = (double*)malloc(sizeof(double) * (size_t)(q > 0 ? q : 1) * p);
+  if (q > 0) oracle_gram(n, q, Q, p, W, Cm);
+  int kept = 0;
+  for (int j = 0; j < p; ++j) {
+    const double worst = q > 0 ? max_abs(q, Cm + (size_t)j * q) : 0.0;
+    const double bn = sqrt(fabs(pairwise_dot(W + (size_t)j * n, BW + (size_t)j * n, n)));
+    if (worst <= sqrt(tau) && fabs(bn - 1.0) <= sqrt(tau)) {
+      if (kept != j) {
+        memcpy(W + (size_t)kept * n, W + (size_t)j * n, sizeof(double) * n);
+        memcpy(BW + (size_t)kept * n, BW + (size_t)j * n, sizeof(double) * n);
+      }
+      ++kept;
+    }
+  }
+  free(Cm);
+  return kept;
+}
+
+/* R = AX - BX diag(lambda), norms and convergence flags. */
+static void residuals_gen(int64_t n, int m, const double* AX, const double* BX, const double* lam, double* R,
+                          double* nrm, int* conv, double tol, int tol_kind) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i)
+    for (int j = 0; j < m; ++j)
+      R[i + (int64_t)j * n] = AX[i + (int64_t)j * n] - lam[j] * BX[i + (int64_t)j * n];
+  for (int j = 0; j < m; ++j) conv[j] = column_converged(n, R + (int64_t)j * n, tol, tol_kind, &nrm[j]);
+}
+
+/* W~ = T R over the active columns with T = (diag(A) - theta diag(B))^{-1}, guarded (R6). */
+static void precondition_gen(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+                             const double* dA, const double* dB, int precond, double* W) {
+  for (int c = 0; c < m_act; ++c) {
+    const int j = m_conv + c;
+    const double* r = R + (int64_t)j * n;
+    double* w = W + (int64_t)c * n;
+    const double floor_ = 1e-8 * fmax(1.0, fabs(lam[j]));
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; ++i) {
+      if (precond == 1) {
+        double delta = dA[i] - lam[j] * dB[i];
+        if (fabs(delta) < floor_) delta = (delta >= 0.0 ? 1.0 : -1.0) * floor_;
+        w[i] = r[i] / delta;
+      } else {
+        w[i] = r[i];
+      }
+    }
+  }
+}
+
+int oracle_lobpcg_gen(const oracle_matrix* A, const oracle_matrix* B, const double* dA, const double* dB,
+                      const oracle_opts* opt, const double* X0, double* evals, double* evecs, double* resnorms,
+                      oracle_info* info, oracle_history* hist) {
+  const int64_t n = A->n;
+  const int k = opt->k, m = opt->k + opt->extra;
+  const double tau = opt->tau > 0 ? opt->tau : 1e-14;
+  const int cap = opt->ortho_cap > 0 ? opt->ortho_cap : 6;
+  const int cap2 = opt->ortho2_cap > 0 ? opt->ortho2_cap : 4;
+  oracle_info loc;
+  memset(&loc, 0, sizeof loc);
+  if (!B || B->n != n || k < 1 || opt->extra < 0 || 3 * (int64_t)m > n || !X0 || !evals || !evecs || !resnorms)
+    return ORACLE_EINVAL;
+  if (opt->precond == 1 && (!dA || !dB)) return ORACLE_EINVAL;
+  if (hist) hist->rows = 0;
+  const int smax = 3 * m;
+  const size_t blk = sizeof(double) * (size_t)n * m;
+  double *X = malloc(blk), *AX = malloc(blk), *BX = malloc(blk), *W = malloc(blk), *AW = malloc(blk);
+  double *BW = malloc(blk), *P = malloc(blk), *AP = malloc(blk), *BP = malloc(blk), *R = malloc(blk);
+  double* Q = malloc(2 * blk);
+  double *V = malloc(sizeof(double) * n * smax), *AV = malloc(sizeof(double) * n * smax);
+  double* BV = malloc(sizeof(double) * n * smax);
+  double *a = malloc(sizeof(double) * smax * smax), *U = malloc(sizeof(double) * smax * smax);
+  double *lam_all = malloc(sizeof(double) * smax), *lam = malloc(sizeof(double) * m);
+  double *up = malloc(sizeof(double) * smax * m), *nrm = malloc(sizeof(double) * m);
+  int* conv = malloc(sizeof(int) * m);
+  int status = ORACLE_ENOCONV;
+  int m_conv = 0, m_act = m, have_p = 0, it = 0, w_cols = 0;
+
+  /* ---- initialisation: B-orthonormal X0 (R20), Rayleigh-Ritz, residual ---- */
+  memcpy(X, X0, blk);
+  oracle_apply(B, m, X, BX);
+  b_ortho(n, m, X, BX, tau, cap, &loc);
+  oracle_apply(A, m, X, AX);
+  loc.spmm_columns += m;
+  oracle_gram(n, m, X, m, AX, a);
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < j; ++i) a[i + j * m] = a[j + i * m] = 0.5 * (a[i + j * m] + a[j + i * m]);
+  oracle_jacobi_eig(m, a, lam, U);
+  memcpy(V, X, blk), memcpy(AV, AX, blk), memcpy(BV, BX, blk);
+  block_times_small(n, m, V, m, U, X);
+  block_times_small(n, m, AV, m, U, AX);
+  block_times_small(n, m, BV, m, U, BX);
+  residuals_gen(n, m, AX, BX, lam, R, nrm, conv, opt->tol, opt->tol_kind);
+  while (m_conv < m && conv[m_conv]) ++m_conv;
+  m_act = m - m_conv;
+  record(hist, m, lam, nrm, m_act, 0, 0);
+  if (m_conv >= k) {
+    status = ORACLE_OK;
+    goto done;
+  }
+  for (it = 1;; ++it) {
+    /* W = B-ortho(ortho(T R, orth(B X, B P))), B W re-used (Sec. 3.3) */
+    precondition_gen(n, m_conv, m_act, R, lam, dA, dB, opt->precond, W);
+    const int q = m + have_p;
+    memcpy(Q, BX, blk);
+    memcpy(Q + (size_t)n * m, BP, sizeof(double) * (size_t)n * have_p);
+    const int hits0 = loc.cap_hits;
+    run_ortho(n, q, Q, tau, cap, opt->trim, &loc);                        /* Q = orth(BX, BP) (R19) */
+    run_ortho_against(n, m_act, W, q, Q, tau, cap, cap2, opt->trim, &loc); /* W^ = ortho(W~, Q) */
+    oracle_apply(B, m_act, W, BW);                                         /* B W^ */
+    b_ortho(n, m_act, W, BW, tau, cap, &loc);                              /* W = W^ L^{-T}, BW re-used */
+    w_cols = m_act;
+    if (loc.cap_hits > hits0) w_cols = drop_gen(n, m_act, W, BW, q, Q, tau); /* R16 */
+    loc.w_dropped += m_act - w_cols;
+    oracle_apply(A, w_cols, W, AW);
+    loc.spmm_columns += w_cols;
+    if (it > opt->maxiter) break;
+    /* ---- Rayleigh-Ritz on V = (X, W, P) ---- */
+    const int s = m + w_cols + have_p;
+    memcpy(V, X, blk), memcpy(AV, AX, blk), memcpy(BV, BX, blk);
+    memcpy(V + n * m, W, sizeof(double) * n * w_cols);
+    memcpy(AV + n * m, AW, sizeof(double) * n * w_cols);
+    memcpy(BV + n * m, BW, sizeof(double) * n * w_cols);
+    memcpy(V + n * (m + w_cols), P, sizeof(double) * n * have_p);
+    memcpy(AV + n * (m + w_cols), AP, sizeof(double) * n * have_p);
+    memcpy(BV + n * (m + w_cols), BP, sizeof(double) * n * have_p);
+    oracle_gram(n, s, V, s, AV, a);
+    for (int j = 0; j < s; ++j)
+      for (int i = 0; i < j; ++i) a[i + j * s] = a[j + i * s] = 0.5 * (a[i + j * s] + a[j + i * s]);
+    oracle_jacobi_eig(s, a, lam_all, U);
+    memcpy(lam, lam_all, sizeof(double) * m);
+    block_times_small(n, s, V, m, U, X);
+    block_times_small(n, s, AV, m, U, AX);
+    block_times_small(n, s, BV, m, U, BX);
+    residuals_gen(n, m, AX, BX, lam, R, nrm, conv, opt->tol, opt->tol_kind);
+    m_conv = 0;
+    while (m_conv < m && conv[m_conv]) ++m_conv;
+    m_act = m - m_conv;
+    record(hist, m, lam, nrm, m_act, w_cols, have_p);
+    if (m_conv >= k) {
+      status = ORACLE_OK;
+      break;
+    }
+    if (it >= opt->maxiter) break;
+    /* P coefficients in R^s, as in Algorithm 1 (R8, R14, R16) */
+    int p_cols = 0;
+    for (int c = 0; c < m_act; ++c) {
+      const int j = m_conv + c;
+      double* col = up + (size_t)p_cols * s;
+      memcpy(col, U + (size_t)j * s, sizeof(double) * s);
+      col[j] -= 1.0;
+      double* proj = (double*)malloc(sizeof(double) * s);
+      memcpy(proj, col, sizeof(double) * s);
+      for (int qq = 0; qq < m; ++qq) {
+        double d = 0.0;
+        for (int i = 0; i < s; ++i) d += U[i + (size_t)qq * s] * col[i];
+        for (int i = 0; i < s; ++i) proj[i] -= d * U[i + (size_t)qq * s];
+      }
+      double pn = 0.0;
+      for (int i = 0; i < s; ++i) pn += proj[i] * proj[i];
+      free(proj);
+      if (sqrt(pn) > 1e-200) ++p_cols;
+    }
+    loc.p_dropped += m_act - p_cols;
+    if (p_cols > 0) {
+      const int hp = loc.cap_hits, asked = p_cols;
+      oracle_ortho_against(s, p_cols, up, m, U, tau, cap, cap2, &loc.shifts, &loc.svqb, &loc.cap_hits,
+                           &loc.cholqr_passes_max);
+      if (loc.cap_hits > hp) p_cols = oracle_drop_unorthogonal_columns(s, p_cols, up, m, U, tau, 1);
+      loc.p_dropped += asked - p_cols;
+    }
+    block_times_small(n, s, V, p_cols, up, P);
+    block_times_small(n, s, AV, p_cols, up, AP);
+    block_times_small(n, s, BV, p_cols, up, BP);
+    have_p = p_cols;
+  }
+  if (it > opt->maxiter) it = opt->maxiter;
+
+done:
+  loc.iterations = it;
+  loc.converged = m_conv;
+  {
+    /* outputs: x^T B x = 1, largest |entry| positive, fresh residual A x - lambda B x */
+    double* Bx = (double*)malloc(blk);
+    double* Ax = (double*)malloc(blk);
+    oracle_apply(B, k, X, Bx);
+    for (int j = 0; j < k; ++j) {
+      const double* x = X + (int64_t)j * n;
+      double big = 0.0;
+      int64_t at = 0;
+      for (int64_t i = 0; i < n; ++i)
+        if (fabs(x[i]) > big) big = fabs(x[i]), at = i;
+      const double sgn = x[at] < 0.0 ? -1.0 : 1.0;
+      const double bn = sqrt(pairwise_dot(x, Bx + (int64_t)j * n, n));
+      for (int64_t i = 0; i < n; ++i) evecs[i + (int64_t)j * n] = sgn * x[i] / bn;
+      evals[j] = lam[j];
+    }
+    oracle_apply(A, k, evecs, Ax);
+    oracle_apply(B, k, evecs, Bx);
+    for (int j = 0; j < k; ++j) {
+      double* r = Ax + (int64_t)j * n;
+      for (int64_t i = 0; i < n; ++i) r[i] -= evals[j] * Bx[i + (int64_t)j * n];
+      resnorms[j] = sqrt(pairwise_dot(r, r, n));
+    }
+    free(Bx), free(Ax);
+  }
+  if (info) *info = loc;
+  free(X), free(AX), free(BX), free(W), free(AW), free(BW), free(P), free(AP), free(BP), free(R), free(Q);
+  free(V), free(AV), free(BV), free(a), free(U), free(lam_all), free(lam), free(up), free(nrm), free(conv);
+  return status;
+}

@@ -139,6 +139,15 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
                   const double* X0, double* evals, double* evecs, double* resnorms,
                   oracle_info* info, oracle_history* hist);
 
+/* Algorithm 1 for the generalised problem A x = lambda B x (Sec. 3.3), B symmetric
+ * positive definite: B-orthonormal basis, B V carried along, W^ = ortho(W~, (B X, B P))
+ * then Cholesky-QR in the B product with re-use of B W^.  dA, dB: diagonals of A and B
+ * (preconditioner (dA - theta dB)^{-1}).  Outputs as oracle_lobpcg with x^T B x = 1 and
+ * resnorms = ||A x - lambda B x||_2. */
+int oracle_lobpcg_gen(const oracle_matrix* A, const oracle_matrix* B, const double* dA, const double* dB,
+                      const oracle_opts* opt, const double* X0, double* evals, double* evecs, double* resnorms,
+                      oracle_info* info, oracle_history* hist);
+
 /* Number of OpenMP threads the oracle runs with (1 without OpenMP). */
 int oracle_threads(void);
 

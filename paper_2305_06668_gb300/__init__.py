@@ -41,7 +41,8 @@ class _Options(C.Structure):
     _fields_ = [("extra", C.c_int), ("maxiter", C.c_int), ("tol_kind", C.c_int), ("precond", C.c_int),
                 ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
                 ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
-                ("mixed_switch", C.c_double), ("autotune", C.c_int), ("ortho_trim", C.c_int)]
+                ("mixed_switch", C.c_double), ("autotune", C.c_int), ("ortho_trim", C.c_int),
+                ("df_products", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -55,7 +56,7 @@ class _Info(C.Structure):
                 ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64),
                 ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int), ("w_dropped", C.c_int),
                 ("p_dropped", C.c_int), ("ortho_grams", C.c_int), ("skipped_recheck", C.c_int),
-                ("skipped_test", C.c_int)]
+                ("skipped_test", C.c_int), ("df_products", C.c_int)]
 
 
 def library_path() -> pathlib.Path:
@@ -75,7 +76,8 @@ def lib():
                      "lobpcg_mlp_backward", "lobpcg_mlp_loss", "lobpcg_mlp_adam", "lobpcg_precond_features",
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
                      "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32",
-                     "lobpcg_probe_fma_rate"):
+                     "lobpcg_probe_fma_rate", "lobpcg_gram_f64_df", "lobpcg_update_f64_df",
+                     "lobpcg_spmm_csr_f64_df"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -143,7 +145,7 @@ class Solver:
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
                  mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
-                 ortho_trim: bool = True, stream=None):
+                 ortho_trim: bool = True, df_products: int = 0, stream=None):
         torch = _torch()
         L = lib()
         self._keep = [diag, row_ptr, col_idx, val, dense]
@@ -170,6 +172,7 @@ class Solver:
         o.mixed_switch = mixed_switch
         o.autotune = 1 if autotune else 0
         o.ortho_trim = 1 if ortho_trim else 0
+        o.df_products = int(df_products)
         w = None
         if mlp_weights is not None:
             w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
@@ -320,6 +323,60 @@ def probe_fma_rate(fp64: bool = True, stream=None) -> float:
     out = C.c_double(0.0)
     _check(lib().lobpcg_probe_fma_rate(C.c_int(1 if fp64 else 0), C.byref(out), _stream(stream)))
     return out.value
+
+
+def spmm_csr_df(row_ptr, col_idx, val, X, Y=None, stream=None):
+    """Y = A X (CSR A, FP64 row-major X) in double-float arithmetic (the refinement's product)."""
+    torch = _torch()
+    n, p = X.shape
+    if Y is None:
+        Y = torch.empty_like(X)
+    _check(lib().lobpcg_spmm_csr_f64_df(C.c_int64(n), _ptr(row_ptr), _ptr(col_idx), _ptr(val),
+                                        C.c_int64(val.numel()), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), _ptr(Y),
+                                        C.c_int(Y.stride(0)), _stream(stream)))
+    return Y
+
+
+def gram_df(X, Y, stream=None):
+    """C = X^T Y of FP64 row-major CUDA blocks (one aligned row stride) in double-float
+    arithmetic (the FP64 refinement's Gram)."""
+    torch = _torch()
+    n, p = X.shape
+    q = Y.shape[1]
+    Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)
+    _check(lib().lobpcg_gram_f64_df(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q), _ptr(Y),
+                                    C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
+    return Cm.t()
+
+
+def update_f64_df(V, U, q=None, alpha=1.0, AV=None, base=None, X=None, AX=None, lam=None, resnorm=False,
+                  stream=None):
+    """FP64 block update X = base + alpha [V_0 ..] U (and AX, residual norms) in double-float
+    arithmetic; the FP64 counterpart of update_f32 (same arguments, float64 blocks)."""
+    torch = _torch()
+    V = list(V)
+    n = V[0].shape[0]
+    ws = [int(v.shape[1]) for v in V]
+    ld = int(V[0].stride(0))
+    q = int(U.shape[1]) if q is None else int(q)
+    if X is None:
+        X = torch.empty((n, q), dtype=torch.float64, device=V[0].device)
+    if AV is not None and AX is None:
+        AX = torch.empty_like(X)
+    Ucol = U if (U.stride(0) == 1 and U.stride(1) == U.shape[0]) else U.t().contiguous().t()
+    vp = (C.c_void_p * len(V))(*[v.data_ptr() for v in V])
+    ap = (C.c_void_p * len(V))(*[a.data_ptr() for a in AV]) if AV is not None else None
+    warr = (C.c_int * len(V))(*ws)
+    rn = (C.c_double * q)() if resnorm else None
+    _check(lib().lobpcg_update_f64_df(C.c_int64(n), C.c_int(len(V)), vp, ap, warr, C.c_int(ld), _ptr(Ucol),
+                                      C.c_int(q), C.c_double(alpha), _ptr(base),
+                                      C.c_int(base.stride(0) if base is not None else 0), _ptr(X), _ptr(AX),
+                                      C.c_int(X.stride(0)), _ptr(lam), rn, _stream(stream)))
+    if AV is None:
+        return X
+    if resnorm:
+        return X, AX, np.array(rn[:])
+    return X, AX
 
 
 def gram_noalloc(X, Y, out=None, stream=None):

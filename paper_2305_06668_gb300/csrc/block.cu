@@ -9,6 +9,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace lobpcg {
 namespace {
@@ -224,6 +225,122 @@ __global__ void __launch_bounds__(256) update_kernel(int64_t n, UpdateJob<T> job
   }
 }
 
+// ---------------------------------------------------------- block update, double-float
+// The FP64 update out_t = base_t + alpha * in_t * U formed on the FP32 pipes (dfloat.cuh):
+// alpha U is split once per CTA into (hi, lo) pairs, each staged row element is split on
+// its way into shared memory, every output element is a compensated double-float sum of
+// its s products plus the base term, widened to FP64 once.  Thread layout, staging and
+// the residual-norm epilogue (in FP64) are those of update_kernel.
+template <int R>
+__device__ __forceinline__ void stage_rows_split(const Cols<double>& c, int64_t r0, int64_t rend, float2* s, int sld) {
+  int off = 0;
+  for (int g = 0; g < c.nseg; ++g) {
+    const int w = c.w[g];
+    const double* p = c.p[g];
+    const int ld = c.ld[g];
+    for (int e = threadIdx.x; e < R * w; e += blockDim.x) {
+      const int r = e / w, j = e - r * w;
+      const int64_t row = r0 + r;
+      s[r * sld + off + j] = row < rend ? df_split(p[row * ld + j]) : make_float2(0.f, 0.f);
+    }
+    off += w;
+  }
+}
+
+template <int CJ, int R>
+__global__ void __launch_bounds__(256) update_df_kernel(int64_t n, UpdateJob<double> job,
+                                                        const double* __restrict__ U, int s, int q,
+                                                        double alpha, const double* __restrict__ lam,
+                                                        double* __restrict__ norm_part, int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int qpad = (q + CJ - 1) / CJ * CJ;
+  float2* sU = reinterpret_cast<float2*>(smem_raw);  // s x qpad, row-major: alpha U split
+  float2* sIn = sU + s * qpad;                       // nprod x R x s
+  double* sNorm = reinterpret_cast<double*>(sIn + job.nprod * R * s);  // [rows_per_pass][2*qpad]
+  const bool unit = job.unit_base != 0;
+  for (int e = threadIdx.x; e < s * qpad; e += blockDim.x) {
+    const int l = e / qpad, j = e % qpad;
+    sU[e] = j < q ? df_split(alpha * U[l + j * s] - (unit && l == j ? 1.0 : 0.0)) : make_float2(0.f, 0.f);
+  }
+  const int tpr = qpad / CJ;
+  const int rows_per_pass = blockDim.x / tpr;
+  const int rr = threadIdx.x / tpr, cj = threadIdx.x % tpr;
+  const bool active = rr < rows_per_pass;
+  double nsum[CJ], nmax[CJ];
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) nsum[j] = 0.0, nmax[j] = 0.0;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += R) {
+    __syncthreads();
+    for (int t = 0; t < job.nprod; ++t) stage_rows_split<R>(job.in[t], r0, r_end, sIn + t * R * s, s);
+    __syncthreads();
+    if (!active) continue;
+    for (int r = rr; r < R; r += rows_per_pass) {
+      const int64_t row = r0 + r;
+      if (row >= r_end) break;
+      double res[2][CJ];
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        if (t >= job.nprod) break;
+        DfAcc acc[CJ];
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) df_zero(acc[j]);
+        const float2* x = sIn + (t * R + r) * s;
+        for (int l = 0; l < s; ++l) {
+          const float2 xv = x[l];
+#pragma unroll
+          for (int j = 0; j < CJ; ++j) df_fma(acc[j], xv, sU[l * qpad + cj * CJ + j]);
+        }
+        double* o = job.out[t] + row * job.ld_out[t];
+        // the base is added in FP64 (one add per output): a base re-rounded to a float
+        // pair would lose its bits past 2^-47 (e.g. the part of W along Y in W - Y C)
+        const double* b = unit ? job.in[0].p[0] + row * job.in[0].ld[0]
+                               : (job.base[t] ? job.base[t] + row * job.ld_base[t] : nullptr);
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          const int col = cj * CJ + j;
+          double v = df_value(acc[j]);
+          if (b && col < q) v = b[col] + v;
+          res[t][j] = v;
+          if (col < q) o[col] = v;
+        }
+      }
+      if (norm_part) {
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) {
+          const int col = cj * CJ + j;
+          if (col < q) {
+            const double rij = fma(-lam[col], res[0][j], res[1][j]);  // AX - lam X, one rounding
+            nsum[j] = fma(rij, rij, nsum[j]);
+            nmax[j] = fmax(nmax[j], fabs(rij));
+          }
+        }
+      }
+    }
+  }
+  if (!norm_part) return;
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      sNorm[rr * 2 * qpad + cj * CJ + j] = nsum[j];
+      sNorm[rr * 2 * qpad + qpad + cj * CJ + j] = nmax[j];
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < q; col += blockDim.x) {
+    double s2 = 0.0, mx = 0.0;
+    for (int g = 0; g < rows_per_pass; ++g) {
+      s2 += sNorm[g * 2 * qpad + col];
+      mx = fmax(mx, sNorm[g * 2 * qpad + qpad + col]);
+    }
+    norm_part[(int64_t)blockIdx.x * 2 * q + col] = s2;
+    norm_part[(int64_t)blockIdx.x * 2 * q + q + col] = mx;
+  }
+}
+
 template <class T>
 __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __restrict__ AX, int ld,
                                const double* __restrict__ lam, int c0, int a,
@@ -398,6 +515,30 @@ int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, in
   const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
   ctas = std::max<int64_t>(1, ceil_div(n, rpc));
   update_kernel<T, CJ, R><<<(unsigned)ctas, threads, smem, st>>>(n, job, U, s, q, alpha, lam, norm_part, rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
+int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, int s, int q, double alpha,
+                     const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  if (q <= 0 || n <= 0) return 0;
+  constexpr int CJ = 4, R = 32;
+  const int qpad = round_up(q, CJ);
+  const int threads = 256;
+  const int tpr = qpad / CJ;
+  const int rows_per_pass = threads / tpr;
+  const size_t smem = (size_t)s * qpad * sizeof(float2) + (size_t)job.nprod * R * s * sizeof(float2) +
+                      (norm_part ? (size_t)rows_per_pass * 2 * qpad * sizeof(double) : 0) + 16;
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(update_df_kernel<CJ, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    return true;
+  }();
+  (void)attr;
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  update_df_kernel<CJ, R><<<(unsigned)ctas, threads, smem, st>>>(n, job, U, s, q, alpha, lam, norm_part, rpc);
   LB_LAUNCH_CHECK();
   return (int)ctas;
 }

@@ -142,6 +142,9 @@ void reduce_partials(const double* part, int nparts, int count, double* out, cud
 // in_t: Cols of width s; out_t/base_t row-major (ld).  base_t may be null (then 0).
 // When norm_part != null (nprod == 2, out0 = X, out1 = AX): also accumulates per-column
 // partial sums of r_ij^2 and max |r_ij| with r = AX - X diag(lam) into norm_part[cta][2*q].
+// unit_base (FP64 double-float path only): out = in + in (U - I) for an in-place square
+// right-multiply (s == q, one segment), so the unchanged part of in is carried in FP64 and
+// only the correction is formed from float pairs; the FP64 FMA path computes in U.
 template <class T>
 struct UpdateJob {
   Cols<T> in[2];
@@ -150,10 +153,26 @@ struct UpdateJob {
   const T* base[2];
   int ld_base[2];
   int nprod;
+  int unit_base;
 };
 template <class T>
 int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
                   const double* lam, double* norm_part, int max_ctas, cudaStream_t st);
+
+// The same FP64 products formed in double-float arithmetic on the FP32 pipes (FP64 data,
+// FP64 results; every product and sum error-compensated, see dfloat.cuh).
+// gram_partials_df returns 0 without launching when the operands do not share one
+// aligned row stride.
+int gram_partials_df(int64_t n, const Cols<double>& a, const Cols<double>& b, bool upper, double* part,
+                     int max_ctas, cudaStream_t st);
+int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, int s, int q, double alpha,
+                     const double* lam, double* norm_part, int max_ctas, cudaStream_t st);
+// dst[i] = (hi, lo) split of src[i] (the double-float operands: matrix values, blocks).
+void launch_split_df(int64_t count, const double* src, float2* dst, cudaStream_t st);
+// Y = A X (FP64 result) from the split values vs (nnz) and the split block Xs (n x ldx
+// pairs, row-major, ldx even, p <= 32); Y row-major FP64 (ldy even).
+void launch_spmm_csr_df(int64_t n, const int64_t* rp, const int32_t* ci, const float2* vs, int p,
+                        const float2* Xs, int ldx, double* Y, int ldy, cudaStream_t st);
 
 // W~_ij = R_ij / guard(d_i - lam_{c0+j}) (precond 1) or R_ij (precond 0) with
 // R = AX[:, c0+j] - lam_{c0+j} X[:, c0+j], j < a.

@@ -43,6 +43,13 @@ const char* set_thread_error(const std::string& msg) {
 
 namespace {
 
+// Orthogonality threshold of the FP64 phases with double-float products (reading R21):
+// their products are good to ~2^-47 relative, so ||X^T X - I|| and ||Y^T X|| can be
+// certified to about 1e-13, not to FP64's 1e-14; 1e-12 keeps the basis orthonormal far
+// below what the residual tolerance needs (an error d in V^T V moves Ritz values by
+// ~d ||A||, 1e-12 x 2000 = 2e-9 for tol 1e-8 on the CI-like workload).
+constexpr double kTauDf = 1e-12;
+
 struct DevBuf {
   void* p = nullptr;
   size_t bytes = 0;
@@ -249,6 +256,7 @@ struct lobpcg_ctx {
   int band = -1;  // CSR: half-width holding most non-zeros (shared-memory window of the product)
 
   DevBuf val32, dense32;  // FP32 copies for the mixed form
+  DevBuf val_df, xs_df;   // (hi, lo) float pairs of the CSR values and of a product's input block
   // mixed form, CSR with a band: the FP32 matrix split into the band part (|col - row| <=
   // band, product from a shared-memory window of X) and the long-range rest
   SplitCSR sp;
@@ -273,6 +281,7 @@ struct lobpcg_ctx {
   DevBuf mlp_params, rho;
   float cscale = 0.f;
   bool use_learned = false;  // cleared for the rest of a solve when the residuals stall
+  bool df_on = false;        // FP64 Grams and updates in double-float arithmetic (this phase)
   FILE* trace = nullptr;  // per-iteration JSON lines (LOBPCG_TRACE=path)
   bool trace_orth = false;  // LOBPCG_TRACE_ORTH=1: also trace max |V^T V - I|
 
@@ -331,7 +340,13 @@ int update(lobpcg_ctx& c, const UpdateJob<T>& job, const double* U, int s, int q
            double* norm_part) {
   const bool timed = c.prof.on && sizeof(T) == 8;
   if (timed) c.prof.kmark();
-  const int parts = launch_update<T>(c.A.n, job, U, s, q, alpha, lam, norm_part, c.max_ctas, c.st);
+  int parts;
+  if constexpr (std::is_same<T, double>::value) {
+    parts = c.df_on ? launch_update_df(c.A.n, job, U, s, q, alpha, lam, norm_part, c.max_ctas, c.st)
+                    : launch_update<T>(c.A.n, job, U, s, q, alpha, lam, norm_part, c.max_ctas, c.st);
+  } else {
+    parts = launch_update<T>(c.A.n, job, U, s, q, alpha, lam, norm_part, c.max_ctas, c.st);
+  }
   if (timed) {
     c.prof.kmark();
     c.prof.kflops += 2.0 * (double)c.A.n * s * q * job.nprod;
@@ -393,7 +408,18 @@ template <class T>
 void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
   if (p <= 0) return;
   c.prof.mark(PH_SPMM);
-  spmm_product<T>(c, X, ldx, p, Y, ldy);
+  bool done = false;
+  if constexpr (std::is_same<T, double>::value) {
+    if (c.df_on && c.A.fmt == LOBPCG_CSR && c.val_df.p && !(ldx & 1) && !(ldy & 1)) {
+      // double-float product: split the block once, then the compensated row sums
+      c.xs_df.ensure((size_t)c.A.n * ldx * sizeof(float2));
+      launch_split_df(c.A.n * (int64_t)ldx, X, c.xs_df.as<float2>(), c.st);
+      launch_spmm_csr_df(c.A.n, c.A.row_ptr, c.A.col_idx, c.val_df.as<float2>(), p, c.xs_df.as<float2>(), ldx, Y,
+                         ldy, c.st);
+      done = true;
+    }
+  }
+  if (!done) spmm_product<T>(c, X, ldx, p, Y, ldy);
   c.stats.spmm_columns += p;
   c.stats.spmm_launches += 1;
   if (sizeof(T) == 8) c.stats.spmm_launches64 += 1, c.stats.spmm_columns64 += p;
@@ -403,7 +429,10 @@ void apply_A(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
 template <class T>
 void gram(lobpcg_ctx& c, const Cols<T>& a, const Cols<T>& b, bool upper, double* out) {
   const int pa = a.width(), pb = b.width();
-  const int parts = gram_partials<T>(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
+  int parts = 0;
+  if constexpr (std::is_same<T, double>::value)
+    if (c.df_on) parts = gram_partials_df(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
+  if (!parts) parts = gram_partials<T>(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
   reduce_partials(c.Gpart, parts, pa * pb, out, c.st);
 }
 
@@ -415,6 +444,7 @@ void right_multiply(lobpcg_ctx& c, T* W, int ld, int p, const double* Tm) {
   job.out[0] = W;
   job.ld_out[0] = ld;
   job.nprod = 1;
+  job.unit_base = 1;  // double-float path: W + W (T - I)
   update<T>(c, job, Tm, p, p, 1.0, nullptr, nullptr);
 }
 
@@ -428,9 +458,12 @@ int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap, const double*
           bool* growth_ok = nullptr) {
   if (growth_ok) *growth_ok = false;
   if (p <= 0) return 0;
-  const bool trim = c.opt.ortho_trim != 0;
-  // eps sqrt(q) g <= tau with the unit of the block's arithmetic (reading R18)
-  const double eps = sizeof(T) == 4 ? 1.1920928955078125e-07 : 2.220446049250313e-16;
+  // the estimates assume Grams accurate to a few eps (FP64 or double-float); the FP32
+  // phase's tensor-core Grams summed in FP32 are not, so it runs the printed algorithms
+  const bool trim = c.opt.ortho_trim != 0 && sizeof(T) == 8;
+  // eps sqrt(q) g <= tau with the unit of the products' arithmetic (reading R18):
+  // 2^-46 for double-float (two roundings at 2^-47 of the split), else FP64's
+  const double eps = c.df_on ? 1.4210854715202004e-14 : 2.220446049250313e-16;
   const double g_max = q > 0 ? tau / (eps * std::sqrt((double)q)) : 0.0;
   int passes = 0;
   LB_CUDA(cudaMemsetAsync(c.ictl, 0, 8 * sizeof(int), c.st));
@@ -452,7 +485,7 @@ int ortho(lobpcg_ctx& c, T* W, int ld, int p, double tau, int cap, const double*
     }
     ++passes;
     right_multiply<T>(c, W, ld, p, c.Tm);               // W <- W L^{-T}
-    if (trim && h[6]) {                                 // R17: ||L^{-T}||^2 <= 2, no re-check
+    if (trim && h[6] && 2.0 * eps <= tau) {             // R17: ||L^{-T}||^2 <= 2, no re-check
       c.stats.skipped_recheck++;
       break;
     }
@@ -809,6 +842,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->mlp_weights = nullptr;
   opt->autotune = 0;
   opt->ortho_trim = 1;
+  opt->df_products = 0;
   return LOBPCG_OK;
 }
 
@@ -874,6 +908,11 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
         else for (int64_t j = 0; j < A->n; ++j)
           launch_to_float(A->n, A->dense + j * A->ld, c->dense32.as<float>() + j * A->n, c->st);
       }
+    }
+    const bool df_phase = c->opt.precision == LOBPCG_MIXED ? c->opt.df_products >= 0 : c->opt.df_products > 0;
+    if (A->fmt == LOBPCG_CSR && df_phase) {
+      c->val_df.ensure((size_t)std::max<int64_t>(A->nnz, 1) * sizeof(float2));
+      launch_split_df(A->nnz, A->val, c->val_df.as<float2>(), c->st);
     }
     if (c->opt.precond == LOBPCG_PREC_LEARNED) {
       c->mlp_params.ensure(mlp::kNumParams * sizeof(float));
@@ -948,12 +987,17 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       c->x0buf.ensure((size_t)n * m * sizeof(double));
       launch_rows_to_colmajor<float, double>(n, m, b.X[p32.xbuf], b.ld, c->x0buf.as<double>(), c->st);
       launch_colmajor_to_rows<double, double>(n, m, c->x0buf.as<double>(), c->b64.X[0], c->b64.ld, c->st);
-      ph = run_lobpcg<double>(*c, k, m, tol, tau, std::max(1, c->opt.maxiter - p32.iterations), false);
+      c->df_on = c->opt.df_products >= 0;
+      ph = run_lobpcg<double>(*c, k, m, tol, c->df_on ? std::max(tau, kTauDf) : tau,
+                              std::max(1, c->opt.maxiter - p32.iterations), false);
+      c->df_on = false;
       fp64_iters = ph.iterations;
       iters += ph.iterations;
     } else {
       launch_colmajor_to_rows<double, double>(n, m, x0, c->b64.X[0], c->b64.ld, c->st);
-      ph = run_lobpcg<double>(*c, k, m, tol, tau, c->opt.maxiter, false);
+      c->df_on = c->opt.df_products > 0;
+      ph = run_lobpcg<double>(*c, k, m, tol, c->df_on ? std::max(tau, kTauDf) : tau, c->opt.maxiter, false);
+      c->df_on = false;
       iters = fp64_iters = ph.iterations;
     }
     // ---- outputs: normalise, fix signs, fresh residuals ----
@@ -1033,6 +1077,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->ortho_grams = c->stats.ortho_grams;
       info->skipped_recheck = c->stats.skipped_recheck;
       info->skipped_test = c->stats.skipped_test;
+      info->df_products = (c->opt.precision == LOBPCG_MIXED) ? (c->opt.df_products >= 0) : (c->opt.df_products > 0);
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))
@@ -1047,6 +1092,8 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   cudaStreamSynchronize(c->st);
   c->val32.release();
   c->dense32.release();
+  c->val_df.release();
+  c->xs_df.release();
   c->sp.release();
   c->b64.buf.release();
   c->b32.buf.release();
@@ -1095,6 +1142,27 @@ extern "C" lobpcg_status lobpcg_spmm_csr_f64(int64_t n, const int64_t* row_ptr, 
     require(p >= 1 && p <= 32 && ldx >= p && ldy >= p, "lobpcg_spmm_csr_f64: need 1 <= p <= 32, ld >= p");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     launch_spmm_csr<double, double>(n, row_ptr, col_idx, val, p, X, ldx, Y, ldy, st);
+    LB_CUDA(cudaStreamSynchronize(st));
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_spmm_csr_f64_df(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
+                                                const double* val, int64_t nnz, int p, const double* X, int ldx,
+                                                double* Y, int ldy, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 0 && nnz >= 0 && row_ptr && col_idx && val && X && Y, "lobpcg_spmm_csr_f64_df: NULL argument");
+    require(p >= 1 && p <= 32 && ldx >= p && ldy >= p, "lobpcg_spmm_csr_f64_df: need 1 <= p <= 32, ld >= p");
+    require(ldx % 2 == 0 && ldy % 2 == 0 && !(reinterpret_cast<uintptr_t>(X) & 15) &&
+                !(reinterpret_cast<uintptr_t>(Y) & 15),
+            "lobpcg_spmm_csr_f64_df: X and Y must be 16-byte aligned with even row strides");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DevBuf vs, xs;
+    vs.ensure((size_t)std::max<int64_t>(nnz, 1) * sizeof(float2));
+    xs.ensure((size_t)std::max<int64_t>(n, 1) * ldx * sizeof(float2));
+    launch_split_df(nnz, val, vs.as<float2>(), st);
+    launch_split_df(n * (int64_t)ldx, X, xs.as<float2>(), st);
+    launch_spmm_csr_df(n, row_ptr, col_idx, vs.as<float2>(), p, xs.as<float2>(), ldx, Y, ldy, st);
     LB_CUDA(cudaStreamSynchronize(st));
     return LOBPCG_OK;
   });
@@ -1154,6 +1222,64 @@ extern "C" lobpcg_status lobpcg_gram_f64(int64_t n, int p, const double* X, int 
     ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
     gram<double>(s.c, cols1<double>(X, ldx, p), cols1<double>(Y, ldy, q), false, C);
     s.c.sync();
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_gram_f64_df(int64_t n, int p, const double* X, int ldx, int q,
+                                            const double* Y, int ldy, double* C, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && X && Y && C, "lobpcg_gram_f64_df: NULL argument or n < 1");
+    require(p >= 1 && q >= 1 && p <= kMaxS && q <= kMaxS && ldx >= p && ldy >= q,
+            "lobpcg_gram_f64_df: need 1 <= p, q <= 96, ld >= width");
+    require(ldx == ldy && ldx % 2 == 0 && !(reinterpret_cast<uintptr_t>(X) & 15) &&
+                !(reinterpret_cast<uintptr_t>(Y) & 15),
+            "lobpcg_gram_f64_df: X and Y must be 16-byte aligned with one even row stride");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    s.c.df_on = true;
+    gram<double>(s.c, cols1<double>(X, ldx, p), cols1<double>(Y, ldy, q), false, C);
+    s.c.sync();
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_update_f64_df(int64_t n, int nseg, const double* const* V, const double* const* AV,
+                                              const int* w, int ld, const double* U, int q, double alpha,
+                                              const double* base, int ld_base, double* X, double* AX, int ld_out,
+                                              const double* lam, double* resnorm, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && nseg >= 1 && nseg <= 3 && V && w && U && X,
+            "lobpcg_update_f64_df: NULL argument, n < 1 or nseg outside 1..3");
+    require(!AV == !AX, "lobpcg_update_f64_df: AV and AX go together");
+    require(!resnorm || (AV && lam && !base), "lobpcg_update_f64_df: resnorm needs AV, AX, lam and no base");
+    int s = 0;
+    Cols<double> cv{}, ca{};
+    for (int g = 0; g < nseg; ++g) {
+      require(V[g] && (!AV || AV[g]) && w[g] >= 0 && w[g] <= ld, "lobpcg_update_f64_df: NULL segment or w > ld");
+      cv = cols_add<double>(cv, V[g], ld, w[g]);
+      if (AV) ca = cols_add<double>(ca, AV[g], ld, w[g]);
+      s += w[g];
+    }
+    require(s >= 1 && s <= kMaxS && q >= 1 && q <= 32 && ld_out >= q && (!base || ld_base >= q),
+            "lobpcg_update_f64_df: need 1 <= s <= 96, 1 <= q <= 32, ld_out >= q, ld_base >= q");
+    ScratchCtx sc(n, reinterpret_cast<cudaStream_t>(stream));
+    sc.c.df_on = true;
+    UpdateJob<double> job{};
+    job.in[0] = cv, job.in[1] = ca;
+    job.out[0] = X, job.out[1] = AX;
+    job.ld_out[0] = job.ld_out[1] = ld_out;
+    job.base[0] = base;
+    job.ld_base[0] = ld_base;
+    job.nprod = AV ? 2 : 1;
+    const int parts = update<double>(sc.c, job, U, s, q, alpha, resnorm ? lam : nullptr,
+                                     resnorm ? sc.c.npart : nullptr);
+    if (resnorm) {
+      reduce_partials(sc.c.npart, parts, 2 * q, sc.c.G, sc.c.st);
+      LB_CUDA(cudaMemcpyAsync(sc.c.host, sc.c.G, (size_t)q * sizeof(double), cudaMemcpyDeviceToHost, sc.c.st));
+    }
+    sc.c.sync();
+    if (resnorm)
+      for (int j = 0; j < q; ++j) resnorm[j] = std::sqrt(sc.c.host[j]);
     return LOBPCG_OK;
   });
 }
@@ -1316,6 +1442,7 @@ extern "C" lobpcg_status lobpcg_solve_batched(lobpcg_ctx* const* ctxs, int nprob
                                  infos ? &infos[i] : nullptr);
       // only the problems in flight hold block workspace: a finished problem returns its own
       ctxs[i]->b64.buf.release();
+      ctxs[i]->xs_df.release();
       ctxs[i]->b32.buf.release();
       ctxs[i]->x0buf.release();
     }

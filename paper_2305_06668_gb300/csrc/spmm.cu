@@ -12,6 +12,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace lobpcg {
 namespace {
@@ -752,6 +753,83 @@ void csr_rows_dispatch(int64_t n, const int64_t* rp, const int32_t* ci, const V*
   else csr_add_launch<T, V, 4, 4, ACC>(n, rp, ci, val, p, X, ldx, Y, ldy, st);
 }
 
+// ---- FP64 product in double-float arithmetic (the refinement phase, dfloat.cuh) ----
+// Y = A X with A's values and X given as (hi, lo) float pairs (split once: the matrix at
+// create time, X before the product).  A group of L lanes owns a row; each lane holds NV
+// 16-byte vectors (2 columns each) and keeps UNR gathers in flight, as the row-parallel
+// FP64 kernel does.  Each term is a compensated double-float product-sum; Y is FP64.
+template <int L, int NV, int UNR>
+__global__ void __launch_bounds__(256) spmm_csr_df_kernel(int64_t n, const int64_t* __restrict__ rp,
+                                                          const int32_t* __restrict__ ci,
+                                                          const float2* __restrict__ vs, int p,
+                                                          const float2* __restrict__ Xs, int ldx,
+                                                          double* __restrict__ Y, int ldy) {
+  constexpr int G = kWarp / L;
+  const int lane = threadIdx.x & 31;
+  const int g = lane / L, li = lane % L;
+  const int col0 = li * 2 * NV;
+  const bool has_cols = col0 < p;
+  const int64_t groups = (int64_t)gridDim.x * (blockDim.x / kWarp) * G;
+  for (int64_t row = ((int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * G + g; row < n;
+       row += groups) {
+    const int64_t e0 = rp[row], e1 = rp[row + 1];
+    if (!has_cols) continue;
+    DfAcc acc[NV][2];
+#pragma unroll
+    for (int w = 0; w < NV; ++w) df_zero(acc[w][0]), df_zero(acc[w][1]);
+    for (int64_t e = e0; e < e1; e += UNR) {
+      float4 xv[UNR][NV];
+      float2 vv[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const bool valid = e + u < e1;
+        const int c = valid ? ci[e + u] : 0;
+        vv[u] = valid ? vs[e + u] : make_float2(0.f, 0.f);
+        const float4* src = reinterpret_cast<const float4*>(Xs + (int64_t)c * ldx + col0);
+#pragma unroll
+        for (int w = 0; w < NV; ++w)
+          xv[u][w] = (valid && col0 + 2 * w < p) ? __ldg(src + w) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u)
+#pragma unroll
+        for (int w = 0; w < NV; ++w) {
+          df_fma(acc[w][0], vv[u], make_float2(xv[u][w].x, xv[u][w].y));
+          df_fma(acc[w][1], vv[u], make_float2(xv[u][w].z, xv[u][w].w));
+        }
+    }
+    double* yr = Y + row * ldy + col0;
+#pragma unroll
+    for (int w = 0; w < NV; ++w) {
+      const int cw = col0 + 2 * w;
+      if (cw + 2 <= p) {
+        *reinterpret_cast<double2*>(yr + 2 * w) = make_double2(df_value(acc[w][0]), df_value(acc[w][1]));
+      } else if (cw < p) {
+        yr[2 * w] = df_value(acc[w][0]);
+      }
+    }
+  }
+}
+
+__global__ void split_df_kernel(int64_t count, const double* __restrict__ src, float2* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = df_split(src[i]);
+}
+
+template <int L, int NV>
+void csr_df_launch(int64_t n, const int64_t* rp, const int32_t* ci, const float2* vs, int p, const float2* Xs,
+                   int ldx, double* Y, int ldy, cudaStream_t st) {
+  int dev = 0, sms = 152;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256;
+  constexpr int G = kWarp / L;
+  int64_t ctas = std::min<int64_t>(ceil_div(n, (threads / kWarp) * G), (int64_t)sms * 6);
+  if (ctas < 1) ctas = 1;
+  spmm_csr_df_kernel<L, NV, 4><<<(unsigned)ctas, threads, 0, st>>>(n, rp, ci, vs, p, Xs, ldx, Y, ldy);
+  LB_LAUNCH_CHECK();
+}
+
 // ---- band / long-range split of a CSR matrix (once, when the solver is created) ----
 
 // Per row: number of entries with |col - row| <= band (cb) and the rest (cl).
@@ -1090,5 +1168,24 @@ template void launch_spmm_dense<double>(int64_t, const double*, int64_t, int, co
                                         double*, int, cudaStream_t);
 template void launch_spmm_dense<float>(int64_t, const float*, int64_t, int, const float*, int,
                                        float*, int, cudaStream_t);
+
+void launch_split_df(int64_t count, const double* src, float2* dst, cudaStream_t st) {
+  if (count <= 0) return;
+  split_df_kernel<<<(unsigned)std::min<int64_t>(ceil_div(count, 256), 152 * 16), 256, 0, st>>>(count, src, dst);
+  LB_LAUNCH_CHECK();
+}
+
+void launch_spmm_csr_df(int64_t n, const int64_t* rp, const int32_t* ci, const float2* vs, int p,
+                        const float2* Xs, int ldx, double* Y, int ldy, cudaStream_t st) {
+  if (n <= 0 || p <= 0) return;
+  if (p > 32 || (ldx & 1) || (ldy & 1)) throw std::invalid_argument("spmm df: p <= 32 and even row strides required");
+  const int nvec = (p + 1) / 2;  // 16-byte vectors (2 columns) per row
+  if (nvec <= 2) csr_df_launch<1, 2>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+  else if (nvec <= 4) csr_df_launch<2, 2>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+  else if (nvec <= 6) csr_df_launch<2, 3>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+  else if (nvec <= 8) csr_df_launch<4, 2>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+  else if (nvec <= 12) csr_df_launch<4, 3>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+  else csr_df_launch<8, 2>(n, rp, ci, vs, p, Xs, ldx, Y, ldy, st);
+}
 
 }  // namespace lobpcg

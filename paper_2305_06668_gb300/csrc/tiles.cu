@@ -11,6 +11,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 
 namespace lobpcg {
 namespace {
@@ -152,6 +153,126 @@ __global__ void __launch_bounds__(256) gram_pipe_kernel(int64_t n, Cols<T> A, Co
         for (int j = 0; j < TJ; ++j) {
           double& dst = scratch[t * per + i * TJ + j];
           dst = (g == 0 ? 0.0 : dst) + (double)acc[i][j];
+        }
+    }
+    __syncthreads();
+  }
+  double* out = part + (int64_t)blockIdx.x * pa * pb;
+  for (int e = threadIdx.x; e < ntiles * per; e += blockDim.x) {
+    const int tt = e / per, ij = e % per;
+    const int i = tile_i[tt] * TI + ij / TJ, j = tile_j[tt] * TJ + ij % TJ;
+    if (i < pa && j < pb && (!upper || i <= j)) out[i + j * pa] = scratch[e];
+  }
+}
+
+// ------------------------------------------------------------------ Gram, double-float
+// FP64 Gram C = A^T B formed on the FP32 pipes (dfloat.cuh): the staged FP64 rows are
+// split in place into (hi, lo) float pairs (same 8 bytes), each thread sums its TI x TJ
+// tile with the compensated double-float product-sum, and every `flush` chunks the pairs
+// are added to FP64 sums (a few rows' worth of FP64 adds per 100+ rows of products).
+// Tiles, groups and the fixed-order group combination are those of gram_pipe_kernel.
+template <int TI, int TJ, int R, int S>
+__global__ void __launch_bounds__(512) gram_df_kernel(int64_t n, Cols<double> A, Cols<double> B, int ld, int upper,
+                                                      int ntiles, int groups, int flush, double* __restrict__ part,
+                                                      int64_t rows_per_cta) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int lds = padded_ld<double>(ld);
+  const int stageA = A.nseg * R * lds, stageB = B.nseg * R * lds;
+  const int stage = stageA + stageB;
+  double* ring = reinterpret_cast<double*>(smem_raw);
+  __shared__ short tile_i[kMaxS * kMaxS / 16], tile_j[kMaxS * kMaxS / 16];
+  const int pa = A.width(), pb = B.width();
+  const int nti = (pa + TI - 1) / TI, ntj = (pb + TJ - 1) / TJ;
+  if (threadIdx.x == 0) {
+    int idx = 0;
+    for (int tj = 0; tj < ntj; ++tj)
+      for (int ti = 0; ti < nti; ++ti)
+        if (!upper || ti * TI <= tj * TJ + TJ - 1) tile_i[idx] = (short)ti, tile_j[idx] = (short)tj, ++idx;
+  }
+  __syncthreads();
+  const int t = threadIdx.x % ntiles, grp = threadIdx.x / ntiles;
+  const bool active = grp < groups;
+  int offA[TI], offB[TJ];
+#pragma unroll
+  for (int i = 0; i < TI; ++i) offA[i] = col_offset(A, tile_i[t] * TI + i, R, lds);
+#pragma unroll
+  for (int j = 0; j < TJ; ++j) offB[j] = col_offset(B, tile_j[t] * TJ + j, R, lds);
+
+  DfAcc acc[TI][TJ];
+  double sum[TI][TJ];
+#pragma unroll
+  for (int i = 0; i < TI; ++i)
+#pragma unroll
+    for (int j = 0; j < TJ; ++j) df_zero(acc[i][j]), sum[i][j] = 0.0;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  const int nchunks = (int)((r_end - r_begin + R - 1) / R);
+#pragma unroll
+  for (int k = 0; k < S - 1; ++k) {
+    if (k < nchunks) {
+      issue_chunk<double, R>(A, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage);
+      issue_chunk<double, R>(B, ld, lds, r_begin + (int64_t)k * R, r_end, ring + k * stage + stageA);
+    }
+    cp_async_commit();
+  }
+  const int vals = A.nseg + B.nseg;  // segments staged per chunk, each R x ld
+  for (int k = 0; k < nchunks; ++k) {
+    cp_async_wait<S - 2>();
+    __syncthreads();
+    {
+      const int kn = k + S - 1;
+      if (kn < nchunks) {
+        double* dst = ring + (kn % S) * stage;
+        issue_chunk<double, R>(A, ld, lds, r_begin + (int64_t)kn * R, r_end, dst);
+        issue_chunk<double, R>(B, ld, lds, r_begin + (int64_t)kn * R, r_end, dst + stageA);
+      }
+      cp_async_commit();
+    }
+    // split the landed chunk in place: each double becomes its (hi, lo) float pair
+    double* cur = ring + (k % S) * stage;
+    for (int e = threadIdx.x; e < vals * R * ld; e += blockDim.x) {
+      const int g = e / (R * ld), rem = e - g * R * ld;
+      const int r = rem / ld, c = rem - r * ld;
+      double* slot = cur + (size_t)g * R * lds + r * lds + c;
+      const float2 h = df_split(*slot);
+      *reinterpret_cast<float2*>(slot) = h;
+    }
+    __syncthreads();
+    if (active) {
+      const float2* sa = reinterpret_cast<const float2*>(cur);
+      const float2* sb = sa + stageA;
+      for (int r = grp; r < R; r += groups) {
+        float2 a[TI], b[TJ];
+#pragma unroll
+        for (int i = 0; i < TI; ++i) a[i] = offA[i] >= 0 ? sa[offA[i] + r * lds] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int j = 0; j < TJ; ++j) b[j] = offB[j] >= 0 ? sb[offB[j] + r * lds] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < TI; ++i)
+#pragma unroll
+          for (int j = 0; j < TJ; ++j) df_fma(acc[i][j], a[i], b[j]);
+      }
+      if ((k + 1) % flush == 0 || k + 1 == nchunks) {
+#pragma unroll
+        for (int i = 0; i < TI; ++i)
+#pragma unroll
+          for (int j = 0; j < TJ; ++j) sum[i][j] += df_value(acc[i][j]), df_zero(acc[i][j]);
+      }
+    }
+  }
+  cp_async_wait<0>();
+  __syncthreads();
+  double* scratch = reinterpret_cast<double*>(smem_raw);
+  constexpr int per = TI * TJ;
+  for (int g = 0; g < groups; ++g) {
+    if (active && grp == g) {
+#pragma unroll
+      for (int i = 0; i < TI; ++i)
+#pragma unroll
+        for (int j = 0; j < TJ; ++j) {
+          double& dst = scratch[t * per + i * TJ + j];
+          dst = (g == 0 ? 0.0 : dst) + sum[i][j];
         }
     }
     __syncthreads();
@@ -444,8 +565,8 @@ __global__ void __launch_bounds__(256) update_pipe_kernel(int64_t n, UpdateJob<T
         for (int j = 0; j < CJ; ++j) {
           const int col = cg * CJ + j;
           if (col < q) {
-            const T rij = res[1][r][j] - (T)lam[col] * res[0][r][j];
-            nsum[j] += (double)(rij * rij);
+            const T rij = fma(-(T)lam[col], res[0][r][j], res[1][r][j]);  // AX - lam X, one rounding
+            nsum[j] = fma((double)rij, (double)rij, nsum[j]);
             nmax[j] = fmax(nmax[j], (double)fabs(rij));
           }
         }
@@ -908,7 +1029,51 @@ int gram_pipe_launch(int64_t n, const Cols<T>& a, const Cols<T>& b, int ld, bool
   return (int)ctas;
 }
 
+template <int TI, int TJ, int R, int S>
+int gram_df_launch(int64_t n, const Cols<double>& a, const Cols<double>& b, int ld, bool upper, double* part,
+                   int max_ctas, cudaStream_t st) {
+  const int pa = a.width(), pb = b.width();
+  const int ntiles = count_tiles(pa, pb, TI, TJ, upper);
+  const int threads = ntiles > 128 ? 512 : 256;
+  const int groups = std::max(1, threads / ntiles);
+  // about 128 rows per thread between the FP64 flushes of its double-float sums
+  const int flush = std::max(1, 128 * groups / R);
+  const int lds = padded_ld<double>(ld);
+  const size_t ring = (size_t)S * (a.nseg + b.nseg) * R * lds * sizeof(double);
+  const size_t red = (size_t)ntiles * TI * TJ * sizeof(double);
+  const size_t smem = std::max(ring, red);
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(gram_df_kernel<TI, TJ, R, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 200 * 1024));
+    return true;
+  }();
+  (void)attr;
+  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  gram_df_kernel<TI, TJ, R, S><<<(unsigned)ctas, threads, smem, st>>>(n, a, b, ld, upper ? 1 : 0, ntiles, groups,
+                                                                      flush, part, rpc);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
 }  // namespace
+
+// Double-float FP64 Gram partials (same layout and contract as gram_partials_pipe<double>);
+// returns 0 when the operands do not share one aligned row stride or do not fit.
+int gram_partials_df(int64_t n, const Cols<double>& a, const Cols<double>& b, bool upper, double* part,
+                     int max_ctas, cudaStream_t st) {
+  if (a.nseg == 0 || b.nseg == 0) return 0;
+  const int ld = a.ld[0];
+  if (!aligned(a, ld) || !aligned(b, ld)) return 0;
+  const int pa = a.width(), pb = b.width();
+  if (pa > kMaxS || pb > kMaxS) return 0;
+  const size_t ring = (size_t)2 * (a.nseg + b.nseg) * 32 * padded_ld<double>(ld) * sizeof(double);
+  if (ring > 190 * 1024) return 0;
+  if (count_tiles(pa, pb, 4, 4, upper) <= 512) return gram_df_launch<4, 4, 32, 2>(n, a, b, ld, upper, part, max_ctas, st);
+  return 0;
+}
 
 // Pipelined Gram partials; returns 0 (nothing launched) when the operands do not share
 // one aligned row stride, so the caller can use the general kernel instead.

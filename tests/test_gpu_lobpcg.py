@@ -215,7 +215,8 @@ def test_ortho_trims_skip_only_passing_tests(precision):
     """The cost trims of Sec. 3.2 (readings R17, R18) skip re-check and test Grams whose
     outcome the estimates already guarantee.  The kernels are deterministic, so the trimmed
     solve repeats the printed algorithm's solve bit for bit with exactly the skipped Grams
-    fewer, and both match the oracle (which runs the same trims)."""
+    fewer, and both match the oracle (which runs the same trims).  The trims run in the FP64
+    phases only (the mixed form's refinement here)."""
     torch = cuda()
     import paper_2305_06668_gb300 as lb
     a = synth.sparse_ci(n=30_011, seed=11)
