@@ -441,6 +441,75 @@ def run_batched(args):
     return 0
 
 
+def run_small_config(args):
+    """A side line per further configuration (not the headline): cfg1, the n = 4096 sparse
+    problem (k = 4, unit vectors plus N(0, 1e-3) noise), or the dense CASSCF-like problem
+    (n = 8192, rank 256, k = 8).  Each form is solved best-of-`steps` after `warmup` solves:
+    mixed + learned, plain FP64, and the two ablations; the dense product's bandwidth is
+    measured from the profiled phase timings."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_06668_gb300 as lb
+    import synth
+    weights = lb.load_mlp_weights()
+    if args.config == "cfg1":
+        a = synth.sparse_cfg1(n=4096, seed=0)
+        t = lb.upload_csr(a)
+        x0 = torch.from_numpy(synth.diag_guess(a.diag, 4, seed=0)).cuda()
+        k, name = 4, "cfg1: sparse n=4096, 16 couplings per row mirrored, k=4, X0 unit vectors + N(0,1e-3)"
+        mat = t
+        nbytes64 = None
+    else:
+        A, d = synth.dense_casscf(n=8192, seed=0, rank=256)
+        mat = dict(diag=torch.from_numpy(d).cuda(), dense=torch.from_numpy(A).cuda())
+        x0 = torch.from_numpy(synth.diag_guess(d, 8, seed=0)).cuda()
+        k, name = 8, "dense CASSCF-like: n=8192, A = D + U S U^T rank 256, k=8, X0 unit vectors + N(0,1e-3)"
+        nbytes64 = 8192 * 8192 * 8
+    forms = {"mixed_learned": dict(precision=lb.MIXED, precond=lb.PREC_LEARNED, mlp_weights=weights),
+             "fp64": dict(precision=lb.FP64),
+             "fp64_learned": dict(precision=lb.FP64, precond=lb.PREC_LEARNED, mlp_weights=weights),
+             "mixed_diagonal": dict(precision=lb.MIXED)}
+    out = {}
+    for fname, kw in forms.items():
+        s = lb.Solver(**mat, maxiter=3000, profile=True, **kw)
+        for _ in range(args.warmup):
+            s.solve(k, TOL, X0=x0)
+        best = None
+        for _ in range(max(1, args.steps)):
+            r = s.solve(k, TOL, X0=x0)
+            if best is None or r.info["seconds"] < best.info["seconds"]:
+                best = r
+        s.close()
+        i = best.info
+        row = {"seconds": i["seconds"], "iterations": i["iterations"], "fp64_iterations": i["fp64_iterations"],
+               "status": lb.STATUS_NAMES[best.status], "max_resnorm": float(np.max(best.resnorms)),
+               "evals": [float(v) for v in best.evals]}
+        if nbytes64:
+            # dense products: FP64 (n^2 * 8 B of A) in the FP64 phase, FP32 (n^2 * 4 B) in the FP32 one
+            l64, l32 = i["spmm_launches_fp64"], i["spmm_launches"] - i["spmm_launches_fp64"]
+            t64 = i["phase_seconds_fp64"][0]
+            t32 = i["phase_seconds"][0] - t64
+            if l64:
+                row["dense_product_fp64_gbs"] = nbytes64 * l64 / t64 / 1e9
+            if l32:
+                row["dense_product_fp32_gbs"] = nbytes64 / 2 * l32 / t32 / 1e9
+        out[fname] = row
+    ref = out["fp64"]["evals"]
+    for row in out.values():
+        row["eig_max_rel_diff_vs_fp64"] = float(np.max(np.abs(np.array(row["evals"]) - ref) /
+                                                    np.maximum(1, np.abs(ref))))
+    hbm, _ = measured_peaks()
+    line = {"metric": METRIC, "value": out["mixed_learned"]["seconds"], "unit": "s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": False, "dtype": "f32+f64",
+            "data": "synthetic", "config": {"workload": name, "form": "mixed + learned (best of steps)"},
+            "fp64_seconds": out["fp64"]["seconds"],
+            "speedup_vs_fp64": out["fp64"]["seconds"] / out["mixed_learned"]["seconds"], "forms": out,
+            "hbm_peak_gbs": hbm}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -449,8 +518,9 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched"],
-                    help="ci2m: the headline workload; batched: the 256-problem serving workload")
+    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense"],
+                    help="ci2m: the headline workload; batched: the 256-problem serving workload; "
+                         "cfg1 / dense: the n=4096 sparse and n=8192 dense configurations (side lines)")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
@@ -462,6 +532,8 @@ def main():
         ap.error("--n changes the workload: only for --profile runs")
     if args.config == "batched":
         return run_batched(args)
+    if args.config in ("cfg1", "dense"):
+        return run_small_config(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -169,6 +169,19 @@ LOBPCG_API lobpcg_status lobpcg_options_default(lobpcg_options* opt);
 LOBPCG_API lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A, const lobpcg_options* opt,
                             lobpcg_stream stream);
 
+/* Creates a solver context for the generalised problem A x = lambda B x with B symmetric
+ * positive definite (Sec. 3.3).  The basis is kept B-orthonormal with B V carried along;
+ * W~ (preconditioned residuals A x - lambda B x, diagonal (diag A - theta diag B)^-1) is
+ * projected against an orthonormal basis of span(B X, B P) by Algorithms 2 and 3, then
+ * orthonormalised in the B product by Cholesky-QR re-using the one application of B.
+ *   A, B   host structs describing device arrays (borrowed until lobpcg_destroy); B->diag
+ *          must hold diag(B)
+ *   opt    precision LOBPCG_FP64, preconditioner NONE or DIAG, df_products <= 0
+ * lobpcg_solve then returns eigenvectors with x^T B x = 1 and resnorms ||A x - lambda B x||.
+ * Errors: EINVAL (inconsistent B, non-finite entries, unsupported options), ENOMEM, ECUDA. */
+LOBPCG_API lobpcg_status lobpcg_create_gen(lobpcg_ctx** out, const lobpcg_matrix* A, const lobpcg_matrix* B,
+                                           const lobpcg_options* opt, lobpcg_stream stream);
+
 /* Runs Algorithm 1 for the k lowest eigenpairs.
  *   k         1 <= k, 3 (k + extra) <= n
  *   tol       residual tolerance (> 0), see tol_kind

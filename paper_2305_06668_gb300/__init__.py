@@ -138,17 +138,19 @@ class Solver:
 
     CSR: pass ``row_ptr`` (int64), ``col_idx`` (int32), ``val`` (float64) CUDA tensors.
     Dense: pass ``dense`` (float64, n x n, column-major storage or symmetric).
-    ``diag`` (float64, n) is always required.
+    ``diag`` (float64, n) is always required.  ``mass``: the matrix B of a generalised
+    problem A x = lambda B x (Sec. 3.3), a dict with the same keys (row_ptr, col_idx, val or
+    dense, and its diag).
     """
 
     def __init__(self, *, diag, row_ptr=None, col_idx=None, val=None, dense=None, extra: int = 0,
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
                  mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
-                 ortho_trim: bool = True, df_products: int = 0, stream=None):
+                 ortho_trim: bool = True, df_products: int = 0, mass=None, stream=None):
         torch = _torch()
         L = lib()
-        self._keep = [diag, row_ptr, col_idx, val, dense]
+        self._keep = [diag, row_ptr, col_idx, val, dense, mass]
         _need_cuda(diag, torch.float64, "diag")
         n = diag.numel()
         m = _Matrix()
@@ -180,7 +182,24 @@ class Solver:
         self.n, self.extra = n, extra
         self._stream_obj = stream if stream is not None else torch.cuda.current_stream()
         self._ctx = C.c_void_p()
-        _check(L.lobpcg_create(C.byref(self._ctx), C.byref(m), C.byref(o), _stream(self._stream_obj)), None)
+        if mass is None:
+            _check(L.lobpcg_create(C.byref(self._ctx), C.byref(m), C.byref(o), _stream(self._stream_obj)), None)
+        else:
+            mb = _Matrix()
+            _need_cuda(mass["diag"], torch.float64, "mass diag")
+            mb.n, mb.diag = mass["diag"].numel(), mass["diag"].data_ptr()
+            if mass.get("dense") is not None:
+                _need_cuda(mass["dense"], torch.float64, "mass dense")
+                mb.fmt, mb.dense, mb.ld = DENSE, mass["dense"].data_ptr(), n
+            else:
+                for key, dt in (("row_ptr", torch.int64), ("col_idx", torch.int32), ("val", torch.float64)):
+                    _need_cuda(mass[key], dt, "mass " + key)
+                mb.fmt, mb.nnz = CSR, mass["val"].numel()
+                mb.row_ptr, mb.col_idx, mb.val = (mass["row_ptr"].data_ptr(), mass["col_idx"].data_ptr(),
+                                                  mass["val"].data_ptr())
+            L.lobpcg_create_gen.restype = C.c_int
+            _check(L.lobpcg_create_gen(C.byref(self._ctx), C.byref(m), C.byref(mb), C.byref(o),
+                                       _stream(self._stream_obj)), None)
 
     def solve(self, k: int, tol: float = 1e-8, X0=None, raise_on_noconv: bool = False) -> Result:
         torch = _torch()

@@ -248,7 +248,7 @@ __device__ __forceinline__ void stage_rows_split(const Cols<double>& c, int64_t 
 }
 
 template <int CJ, int R>
-__global__ void __launch_bounds__(256) update_df_kernel(int64_t n, UpdateJob<double> job,
+__global__ void __launch_bounds__(256, 3) update_df_kernel(int64_t n, UpdateJob<double> job,
                                                         const double* __restrict__ U, int s, int q,
                                                         double alpha, const double* __restrict__ lam,
                                                         double* __restrict__ norm_part, int64_t rows_per_cta) {
@@ -345,7 +345,7 @@ template <class T>
 __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __restrict__ AX, int ld,
                                const double* __restrict__ lam, int c0, int a,
                                const double* __restrict__ diag, int precond, T* __restrict__ W,
-                               int ldw) {
+                               int ldw, const double* __restrict__ diagB) {
   // a 2-D walk (row, column) without 64-bit divisions: a warp covers 32 / a rows
   const int a_pad = a <= 1 ? 1 : (a <= 2 ? 2 : (a <= 4 ? 4 : (a <= 8 ? 8 : (a <= 16 ? 16 : 32))));
   const int rows_per_block = blockDim.x / a_pad;
@@ -359,7 +359,8 @@ __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __re
     T w = r;
     if (precond == 1) {
       // computed in the block's precision: FP64 path exact, FP32 path keeps the FP64 units free
-      T delta = (T)diag[i] - (T)l;
+      // generalised problem (diagB): X holds B X and the denominator is d_A - theta d_B
+      T delta = diagB ? (T)(diag[i] - l * diagB[i]) : (T)diag[i] - (T)l;
       if (fabs(delta) < fl) delta = delta >= T(0) ? fl : -fl;
       w = r / delta;
     }
@@ -534,7 +535,10 @@ int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, i
     return true;
   }();
   (void)attr;
-  int64_t ctas = std::min<int64_t>(max_ctas, ceil_div(n, R));
+  // three CTAs per SM (registers and shared memory allow it): while one waits at its
+  // staging barrier the others keep the FP32 pipes busy (two per SM left them 60% idle)
+  const int64_t max_df = std::max<int64_t>(max_ctas, 3 * (int64_t)num_sms());
+  int64_t ctas = std::min<int64_t>(max_df, ceil_div(n, R));
   if (ctas < 1) ctas = 1;
   const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
   ctas = std::max<int64_t>(1, ceil_div(n, rpc));
@@ -545,9 +549,10 @@ int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, i
 
 template <class T>
 void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
-                    const double* diag, int precond, T* W, int ldw, cudaStream_t st) {
+                    const double* diag, int precond, T* W, int ldw, cudaStream_t st, const double* diagB) {
   if (a <= 0 || n <= 0) return;
-  precond_kernel<T><<<grid_for(n * a, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, precond, W, ldw);
+  precond_kernel<T><<<grid_for(n * a, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, precond, W, ldw,
+                                                         diagB);
   LB_LAUNCH_CHECK();
 }
 
@@ -586,8 +591,8 @@ template int gram_partials<double>(int64_t, const Cols<double>&, const Cols<doub
 template int gram_partials<float>(int64_t, const Cols<float>&, const Cols<float>&, bool, double*, int, cudaStream_t);
 template int launch_update<double>(int64_t, const UpdateJob<double>&, const double*, int, int, double, const double*, double*, int, cudaStream_t);
 template int launch_update<float>(int64_t, const UpdateJob<float>&, const double*, int, int, double, const double*, double*, int, cudaStream_t);
-template void launch_precond<double>(int64_t, const double*, const double*, int, const double*, int, int, const double*, int, double*, int, cudaStream_t);
-template void launch_precond<float>(int64_t, const float*, const float*, int, const double*, int, int, const double*, int, float*, int, cudaStream_t);
+template void launch_precond<double>(int64_t, const double*, const double*, int, const double*, int, int, const double*, int, double*, int, cudaStream_t, const double*);
+template void launch_precond<float>(int64_t, const float*, const float*, int, const double*, int, int, const double*, int, float*, int, cudaStream_t, const double*);
 template void launch_colmajor_to_rows<double, double>(int64_t, int, const double*, double*, int, cudaStream_t);
 template void launch_colmajor_to_rows<double, float>(int64_t, int, const double*, float*, int, cudaStream_t);
 template void launch_rows_to_colmajor<double, double>(int64_t, int, const double*, int, double*, cudaStream_t);

@@ -93,6 +93,7 @@ struct Stats {
   int w_dropped = 0;
   int p_dropped = 0;
   int ortho_grams = 0, skipped_recheck = 0, skipped_test = 0;
+  int64_t b_products = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -282,6 +283,20 @@ struct lobpcg_ctx {
   float cscale = 0.f;
   bool use_learned = false;  // cleared for the rest of a solve when the residuals stall
   bool df_on = false;        // FP64 Grams and updates in double-float arithmetic (this phase)
+  // generalised problem A x = lambda B x (Sec. 3.3): B (borrowed), B X, B P (double-
+  // buffered like X and P), B W, and Q = orth(B X, B P) for the projection of W~
+  lobpcg_matrix B{};
+  bool gen = false;
+  DevBuf gbuf;
+  double *BX[2]{}, *BP[2]{}, *BW = nullptr, *Q = nullptr;
+  int ldq = 0;
+  void ensure_gen(int64_t n, int ld) {
+    ldq = 2 * ld;
+    const size_t e = (size_t)n * ld;
+    gbuf.ensure(e * 7 * sizeof(double));
+    double* b = gbuf.as<double>();
+    BX[0] = b, BX[1] = b + e, BP[0] = b + 2 * e, BP[1] = b + 3 * e, BW = b + 4 * e, Q = b + 5 * e;
+  }
   FILE* trace = nullptr;  // per-iteration JSON lines (LOBPCG_TRACE=path)
   bool trace_orth = false;  // LOBPCG_TRACE_ORTH=1: also trace max |V^T V - I|
 
@@ -790,6 +805,184 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   return out;
 }
 
+// ============================================ generalised problem (Sec. 3.3), FP64
+// Y = B X for the mass matrix B (CSR or dense, FP64 products).
+void apply_B(lobpcg_ctx& c, const double* X, int ldx, int p, double* Y, int ldy) {
+  if (p <= 0) return;
+  if (c.B.fmt == LOBPCG_CSR)
+    launch_spmm_csr<double, double>(c.A.n, c.B.row_ptr, c.B.col_idx, c.B.val, p, X, ldx, Y, ldy, c.st);
+  else
+    launch_spmm_dense<double>(c.A.n, c.B.dense, c.B.ld, p, X, ldx, Y, ldy, c.st);
+  c.stats.b_products += 1;
+}
+
+// Algorithm 2 in the B product with re-use of B X: M = X^T (B X), stop when ||M - I|| <=
+// tau, else X <- X T and B X <- (B X) T with the Cholesky-QR transform T of M.
+int b_ortho(lobpcg_ctx& c, double* X, double* BXp, int ld, int p, double tau, int cap) {
+  if (p <= 0) return 0;
+  int passes = 0;
+  LB_CUDA(cudaMemsetAsync(c.ictl, 0, 8 * sizeof(int), c.st));
+  const int* h = reinterpret_cast<const int*>(c.host);
+  for (;;) {
+    gram<double>(c, cols1<double>(X, ld, p), cols1<double>(BXp, ld, p), false, c.G);
+    launch_cholqr_small(p, c.G, tau, c.Tm, c.ictl, c.st);
+    LB_CUDA(cudaMemcpyAsync(c.host, c.ictl, 8 * sizeof(int), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    if (h[0]) break;
+    if (passes >= cap) {
+      c.stats.cap_hits++;
+      break;
+    }
+    ++passes;
+    right_multiply<double>(c, X, ld, p, c.Tm);
+    right_multiply<double>(c, BXp, ld, p, c.Tm);
+  }
+  c.stats.shifts += h[1];
+  c.stats.svqb += h[2];
+  c.stats.cholqr_passes_max = std::max(c.stats.cholqr_passes_max, passes);
+  return passes;
+}
+
+// W from W~ (Sec. 3.3): W^ = ortho(W~, Q) with Q = orth(B X, B P) (Algorithms 2 and 3),
+// then Cholesky-QR of W^ in the B product with B W = (B W^) L^{-T}.  Returns the columns
+// kept (reading R16 when a cap was hit).
+int gen_w_step(lobpcg_ctx& c, int m, int pw, int a, double tau, int cap, int cap2, int cur) {
+  Blocks<double>& b = c.b64;
+  const int ld = b.ld;
+  const int64_t n = c.A.n;
+  const int q = m + pw;
+  LB_CUDA(cudaMemcpy2DAsync(c.Q, (size_t)c.ldq * 8, c.BX[cur], (size_t)ld * 8, (size_t)m * 8, (size_t)n,
+                            cudaMemcpyDeviceToDevice, c.st));
+  if (pw > 0)
+    LB_CUDA(cudaMemcpy2DAsync(c.Q + m, (size_t)c.ldq * 8, c.BP[cur], (size_t)ld * 8, (size_t)pw * 8, (size_t)n,
+                              cudaMemcpyDeviceToDevice, c.st));
+  ortho<double>(c, c.Q, c.ldq, q, tau, cap);                            // Q = orth(B X, B P)
+  int aw = a;
+  ortho_against<double>(c, b.W, ld, a, cols1<double>(c.Q, c.ldq, q), tau, cap, cap2, &aw);  // W^
+  apply_B(c, b.W, ld, aw, c.BW, ld);                                    // B W^
+  const int hits0 = c.stats.cap_hits;
+  b_ortho(c, b.W, c.BW, ld, aw, tau, cap);                             // W = W^ L^{-T}, B W re-used
+  if (c.stats.cap_hits > hits0 && aw > 0) {
+    // R16 in the B product: keep the columns with B-norm 1 to sqrt(tau)
+    gram<double>(c, cols1<double>(b.W, ld, aw), cols1<double>(c.BW, ld, aw), false, c.G);
+    std::vector<double> Mh((size_t)aw * aw);
+    LB_CUDA(cudaMemcpyAsync(Mh.data(), c.G, Mh.size() * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    std::vector<double> sel((size_t)aw * aw, 0.0);
+    int k2 = 0;
+    for (int j = 0; j < aw; ++j)
+      if (std::fabs(std::sqrt(std::max(Mh[(size_t)j * aw + j], 0.0)) - 1.0) <= std::sqrt(tau))
+        sel[(size_t)k2 * aw + j] = 1.0, ++k2;
+    if (k2 < aw) {
+      LB_CUDA(cudaMemcpyAsync(c.Tm, sel.data(), sel.size() * sizeof(double), cudaMemcpyHostToDevice, c.st));
+      for (double* blk : {b.W, c.BW}) {
+        if (k2 == 0) break;
+        UpdateJob<double> job{};
+        job.in[0] = cols1<double>(blk, ld, aw);
+        job.out[0] = blk;
+        job.ld_out[0] = ld;
+        job.nprod = 1;
+        update<double>(c, job, c.Tm, aw, k2, 1.0, nullptr, nullptr);
+      }
+      c.stats.w_dropped += aw - k2;
+      aw = k2;
+    }
+  }
+  apply_A<double>(c, b.W, ld, aw, b.AW, ld);                             // A W
+  return aw;
+}
+
+// Algorithm 1 for A x = lambda B x in FP64: B-orthonormal basis, B V carried along.  The
+// residual pair is (B V, A V) u_x, so the fused epilogue gives ||A x - lambda B x||.
+PhaseOut run_lobpcg_gen(lobpcg_ctx& c, int k, int m, double tol, double tau, int maxiter) {
+  Blocks<double>& b = c.b64;
+  c.prof.prec64 = 1;
+  const int64_t n = c.A.n;
+  const int ld = b.ld;
+  const int cap = c.opt.ortho_cap, cap2 = c.opt.ortho2_cap;
+  const int tol_kind = c.opt.tol_kind;
+  const int pc = c.opt.precond == LOBPCG_PREC_NONE ? 0 : 1;
+  PhaseOut out;
+  LockState ls{0, m, 0, 0, 0, 0};
+  LB_CUDA(cudaMemcpyAsync(c.lock, &ls, sizeof ls, cudaMemcpyHostToDevice, c.st));
+  auto read_lock = [&]() {
+    LB_CUDA(cudaMemcpyAsync(c.host, c.lock, sizeof(LockState), cudaMemcpyDeviceToHost, c.st));
+    c.sync();
+    std::memcpy(&ls, c.host, sizeof ls);
+  };
+  // ---- initialisation: B-orthonormal X0 (R20), Rayleigh-Ritz, residual ----
+  apply_B(c, b.X[0], ld, m, c.BX[0], ld);
+  b_ortho(c, b.X[0], c.BX[0], ld, m, tau, cap);
+  apply_A<double>(c, b.X[0], ld, m, b.AX[0], ld);
+  gram<double>(c, cols1<double>(b.X[0], ld, m), cols1<double>(b.AX[0], ld, m), true, c.G);
+  launch_syev(m, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, false, 1e-15);
+  LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+  auto rotate = [&](const Cols<double>& V, const Cols<double>& AV, const Cols<double>& BV, int s, int nxt,
+                    bool with_p) {
+    UpdateJob<double> jx{};
+    jx.in[0] = V, jx.out[0] = b.X[nxt], jx.ld_out[0] = ld, jx.nprod = 1;
+    update<double>(c, jx, c.U, s, m, 1.0, nullptr, nullptr);                 // X = V u_x
+    UpdateJob<double> jp{};
+    jp.in[0] = BV, jp.in[1] = AV;
+    jp.out[0] = c.BX[nxt], jp.out[1] = b.AX[nxt];
+    jp.ld_out[0] = jp.ld_out[1] = ld;
+    jp.nprod = 2;
+    const int parts = update<double>(c, jp, c.U, s, m, 1.0, c.lam, c.npart);  // (BX, AX), ||AX - BX lam||
+    launch_lock_and_p(s, m, k, n, c.npart, parts, c.U, tol, tol_kind, tau, c.lock, c.resnorm, c.colmax, c.up,
+                      with_p, c.st);
+  };
+  rotate(cols1<double>(b.X[0], ld, m), cols1<double>(b.AX[0], ld, m), cols1<double>(c.BX[0], ld, m), m, 1, false);
+  int cur = 1;
+  read_lock();
+  if (ls.done) {
+    out.converged = true, out.m_conv = ls.m_conv, out.xbuf = cur;
+    return out;
+  }
+  int a = ls.m_act, m_conv = ls.m_conv, pw = 0;
+  launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag);
+  int aw = gen_w_step(c, m, 0, a, tau, cap, cap2, cur);
+  int it = 1;
+  for (; it <= maxiter; ++it) {
+    const int s = m + pw + aw;
+    Cols<double> V = cols_add<double>(cols_add<double>(cols1<double>(b.X[cur], ld, m), b.P[cur], ld, pw), b.W, ld, aw);
+    Cols<double> AV =
+        cols_add<double>(cols_add<double>(cols1<double>(b.AX[cur], ld, m), b.AP[cur], ld, pw), b.AW, ld, aw);
+    Cols<double> BV =
+        cols_add<double>(cols_add<double>(cols1<double>(c.BX[cur], ld, m), c.BP[cur], ld, pw), c.BW, ld, aw);
+    gram<double>(c, V, AV, true, c.G);                                      // a = V^T A V
+    launch_syev(s, c.G, true, c.lam_all, c.U, c.ictl + 4, c.st, false, 1e-15);
+    LB_CUDA(cudaMemcpyAsync(c.lam, c.lam_all, m * sizeof(double), cudaMemcpyDeviceToDevice, c.st));
+    const int nxt = cur ^ 1;
+    rotate(V, AV, BV, s, nxt, true);
+    read_lock();
+    if (ls.done) {
+      cur = nxt;
+      out.converged = true;
+      break;
+    }
+    const int a_new = ls.m_act, pw_new = ls.p_cols;
+    c.stats.p_dropped += a_new - pw_new;
+    if (pw_new > 0) {
+      UpdateJob<double> jp{};
+      jp.in[0] = V, jp.out[0] = b.P[nxt], jp.ld_out[0] = ld, jp.nprod = 1;
+      update<double>(c, jp, c.up, s, pw_new, 1.0, nullptr, nullptr);          // P = V u_p
+      UpdateJob<double> jq{};
+      jq.in[0] = BV, jq.in[1] = AV;
+      jq.out[0] = c.BP[nxt], jq.out[1] = b.AP[nxt];
+      jq.ld_out[0] = jq.ld_out[1] = ld;
+      jq.nprod = 2;
+      update<double>(c, jq, c.up, s, pw_new, 1.0, nullptr, nullptr);         // B P, A P
+    }
+    cur = nxt, a = a_new, m_conv = ls.m_conv, pw = pw_new;
+    launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag);
+    aw = gen_w_step(c, m, pw, a, tau, cap, cap2, cur);
+  }
+  out.iterations = std::min(it, maxiter);
+  out.m_conv = ls.m_conv;
+  out.xbuf = cur;
+  return out;
+}
+
 lobpcg_status fail(lobpcg_ctx* c, lobpcg_status s, const std::string& msg) {
   if (c) c->err = msg;
   else g_create_error = msg;
@@ -932,6 +1125,48 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
   return st;
 }
 
+extern "C" lobpcg_status lobpcg_create_gen(lobpcg_ctx** out, const lobpcg_matrix* A, const lobpcg_matrix* B,
+                                           const lobpcg_options* opt, lobpcg_stream stream) {
+  if (out) *out = nullptr;
+  if (!B) return fail(nullptr, LOBPCG_EINVAL, "lobpcg_create_gen: B must not be NULL");
+  lobpcg_options o;
+  if (opt) o = *opt;
+  else lobpcg_options_default(&o);
+  if (o.precision != LOBPCG_FP64 || o.precond == LOBPCG_PREC_LEARNED || o.df_products > 0)
+    return fail(nullptr, LOBPCG_EINVAL,
+                "lobpcg_create_gen: the generalised problem runs in FP64 with the diagonal or no preconditioner");
+  lobpcg_ctx* c = nullptr;
+  lobpcg_status st = lobpcg_create(&c, A, &o, stream);
+  if (st != LOBPCG_OK) return st;
+  st = guarded(nullptr, [&]() -> lobpcg_status {
+    require(B->n == A->n && B->diag != nullptr, "lobpcg_create_gen: B must have A's order and a diagonal");
+    if (B->fmt == LOBPCG_CSR)
+      require(B->row_ptr && B->col_idx && B->val && B->nnz >= 0, "lobpcg_create_gen: CSR arrays of B missing");
+    else if (B->fmt == LOBPCG_DENSE)
+      require(B->dense && B->ld >= B->n, "lobpcg_create_gen: dense B missing or ld < n");
+    else
+      throw InvalidArg("lobpcg_create_gen: unknown format of B");
+    const int one = 1;
+    LB_CUDA(cudaMemcpyAsync(c->ictl + 5, &one, sizeof(int), cudaMemcpyHostToDevice, c->st));
+    if (B->fmt == LOBPCG_CSR) launch_all_finite(B->nnz, B->val, c->ictl + 5, c->st);
+    else for (int64_t j = 0; j < B->n; ++j) launch_all_finite(B->n, B->dense + j * B->ld, c->ictl + 5, c->st);
+    launch_all_finite(B->n, B->diag, c->ictl + 5, c->st);
+    int finite = 0;
+    LB_CUDA(cudaMemcpyAsync(&finite, c->ictl + 5, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    c->sync();
+    require(finite == 1, "lobpcg_create_gen: B or its diagonal has non-finite entries");
+    c->B = *B;
+    c->gen = true;
+    return LOBPCG_OK;
+  });
+  if (st != LOBPCG_OK) {
+    lobpcg_destroy(c);
+    return st;
+  }
+  *out = c;
+  return LOBPCG_OK;
+}
+
 extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const double* X0,
                                       double* evals, double* evecs, double* resnorms,
                                       lobpcg_info* info) {
@@ -975,7 +1210,12 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     PhaseOut ph;
     const double tau = c->opt.tau_ortho;
     autotune_spmm<double>(*c, m, c->b64.W, c->b64.ld, c->b64.AW);
-    if (c->opt.precision == LOBPCG_MIXED) {
+    if (c->gen) {
+      c->ensure_gen(n, c->b64.ld);
+      launch_colmajor_to_rows<double, double>(n, m, x0, c->b64.X[0], c->b64.ld, c->st);
+      ph = run_lobpcg_gen(*c, k, m, tol, tau, c->opt.maxiter);
+      iters = fp64_iters = ph.iterations;
+    } else if (c->opt.precision == LOBPCG_MIXED) {
       c->b32.ensure(n, m);
       autotune_spmm<float>(*c, m, c->b32.W, c->b32.ld, c->b32.AW);
       launch_colmajor_to_rows<double, float>(n, m, x0, c->b32.X[0], c->b32.ld, c->st);
@@ -1004,7 +1244,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     Blocks<double>& b = c->b64;
     const double* X = b.X[ph.xbuf];
     const Cols<double> xk = cols1<double>(X, b.ld, k);
-    gram<double>(*c, xk, xk, false, c->G);
+    // normalisation: x^T x = 1, or x^T B x = 1 for the generalised problem
+    gram<double>(*c, xk, c->gen ? cols1<double>(c->BX[ph.xbuf], b.ld, k) : xk, false, c->G);
     launch_col_sign<double>(n, k, X, b.ld, c->Gpart, c->max_ctas, c->sgn, c->st);
     launch_scale_matrix(k, c->G, c->sgn, c->S, c->st);
     double* Xs = b.P[0];   // scratch blocks (no longer needed)
@@ -1026,8 +1267,11 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       std::vector<double> eye((size_t)k * k, 0.0);
       for (int j = 0; j < k; ++j) eye[(size_t)j * k + j] = 1.0;
       LB_CUDA(cudaMemcpyAsync(c->Tm, eye.data(), eye.size() * sizeof(double), cudaMemcpyHostToDevice, c->st));
+      // the pair (X, AX), or (B X, A X): the epilogue forms A x - lambda x or A x - lambda B x
+      double* BXs = c->gen ? c->BP[0] : nullptr;
+      if (c->gen) apply_B(*c, Xs, b.ld, k, BXs, b.ld);
       UpdateJob<double> job{};
-      job.in[0] = cols1<double>(Xs, b.ld, k);
+      job.in[0] = cols1<double>(c->gen ? BXs : Xs, b.ld, k);
       job.in[1] = cols1<double>(AXs, b.ld, k);
       job.out[0] = b.W, job.out[1] = b.AW;
       job.ld_out[0] = job.ld_out[1] = b.ld;
@@ -1094,6 +1338,7 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   c->dense32.release();
   c->val_df.release();
   c->xs_df.release();
+  c->gbuf.release();
   c->sp.release();
   c->b64.buf.release();
   c->b32.buf.release();
@@ -1443,6 +1688,7 @@ extern "C" lobpcg_status lobpcg_solve_batched(lobpcg_ctx* const* ctxs, int nprob
       // only the problems in flight hold block workspace: a finished problem returns its own
       ctxs[i]->b64.buf.release();
       ctxs[i]->xs_df.release();
+      ctxs[i]->gbuf.release();
       ctxs[i]->b32.buf.release();
       ctxs[i]->x0buf.release();
     }
