@@ -30,16 +30,13 @@ if ROOT not in sys.path:
 
 METRIC = "time to k eigenpairs at \u2016r\u2016\u22641e-8: mixed+learned vs plain FP64 LOBPCG, 1 GB300"
 N_ROWS, K, EXTRA, TOL, SEED = 2_000_000, 16, 5, 1e-8, 0
-# DRAM bytes (read + write) per FP64 block-update launch, averaged over the 52 update
-# launches of two solves in an ncu capture at n = 10^6 (687 MB), scaled to n = 2*10^6 by
-# the rows processed
-UPDATE_FP64_TRAFFIC = 2 * 686.6e6
 WORKLOAD = "CI-like sparse symmetric n=2,000,000, ~65 nnz/row, k=16 (+5 extra), tol 1e-8"
 # Record of one complete oracle solve of this workload (iterations, wall time, threads, the
 # per-iteration time of its first iterations), written by oracle/record_full_solve.py, which
 # calls only the oracle.  Both CPU legs scale it to the machine's cores.
 ORACLE_RECORD = os.path.join(ROOT, "oracle", "records", "ci2m_seed0.json")
 FP64_PEAK_SOURCE = "FP64 FMA rate measured in this run (lobpcg_probe_fma_rate)"
+DF_OPS_PER_TERM = 15  # FP32 operations of one double-float multiply-add (dfloat.cuh df_fma)
 
 
 def log(*a):
@@ -309,18 +306,43 @@ def run_ours(args):
                                   "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
                                   "flops_per_launch": f64, "avg_launch_s": t64,
                                   "peak_source": FP64_PEAK_SOURCE}
-    # the FP64 block update (update_kernel<double>): the kernel with the largest share of GPU
-    # time in the ncu launch list of this command, timed per launch with CUDA events
+    # the FP64 block updates of the refinement, timed per launch with CUDA events.  With
+    # double-float products (the default in the mixed form's refinement) they run on the FP32
+    # pipes: each FP64-equivalent multiply-add is 15 FP32 operations (TwoProduct, TwoSum,
+    # Fast2Sum renormalisation), so the roofline counts FP32 pipe operations (one per issue
+    # slot) against the FP32 FMA instruction rate of this GPU (the probe's FP32 TFLOP/s / 2).
     ut = sum(i["update_fp64_seconds"] for _, i, _, _ in infos)
     uf = sum(i["update_fp64_flops"] for _, i, _, _ in infos)
     ul = sum(i["update_fp64_launches"] for _, i, _, _ in infos)
+    df = bool(infos[-1][1]["df_products"])
     if ul and ut > 0:
-        rooflines["update_fp64"] = {"kernel": "update_kernel<double> (FP64 block updates: X = V u_x, P = V u_p, "
-                                              "W -= Y C, W <- W L^-T)", "bound": "alu",
-                                    "achieved": uf / ut / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                                    "frac": uf / ut / 1e12 / fp64_peak, "traffic": UPDATE_FP64_TRAFFIC,
-                                    "flops_per_launch": uf / ul, "avg_launch_s": ut / ul,
-                                    "peak_source": FP64_PEAK_SOURCE}
+        if df:
+            ops = uf / 2.0 * DF_OPS_PER_TERM
+            rooflines["update_fp64"] = {"kernel": "update_df_kernel (FP64 block updates in double-float on the FP32 "
+                                                  "pipes: X = V u_x, P = V u_p, W -= Y C, W <- W + W (T - I))",
+                                        "bound": "alu", "achieved": ops / ut / 1e12, "peak": fp32_peak / 2,
+                                        "unit": "TFLOP/s", "frac": ops / ut / 1e12 / (fp32_peak / 2),
+                                        "ops": "FP32 pipe operations, 15 per FP64-equivalent multiply-add",
+                                        "fp64_equivalent_tflops": uf / ut / 1e12, "traffic": None,
+                                        "flops_per_launch": ops / ul, "avg_launch_s": ut / ul,
+                                        "peak_source": "FP32 FMA instruction rate measured in this run "
+                                                       "(lobpcg_probe_fma_rate / 2)"}
+        else:
+            rooflines["update_fp64"] = {"kernel": "update_kernel<double> (FP64 block updates)", "bound": "alu",
+                                        "achieved": uf / ut / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                        "frac": uf / ut / 1e12 / fp64_peak, "traffic": None,
+                                        "flops_per_launch": uf / ul, "avg_launch_s": ut / ul,
+                                        "peak_source": FP64_PEAK_SOURCE}
+    # the FP32 Rayleigh-Ritz Grams (tcgen05 kernel): algorithmic bytes 2 n s 4 per Gram over the
+    # FP32 part of the Rayleigh-Ritz Gram phase
+    gb = sum(i["rr_gram32_bytes"] for _, i, _, _ in infos)
+    gc = sum(i["rr_gram32_count"] for _, i, _, _ in infos)
+    gt = ph_all["rr_gram"] - ph64["rr_gram"]
+    if gc and gt > 0:
+        rooflines["gram_fp32"] = {"kernel": "gram_umma_kernel + reduce (V^T AV, FP32, tcgen05 3xTF32)",
+                                  "bound": "hbm", "achieved": gb / gt / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                                  "frac": gb / gt / 1e9 / hbm_peak, "traffic": None, "bytes_per_launch": gb / gc,
+                                  "avg_launch_s": gt / gc, "peak_source": peak_kind}
     share = {k: v / max(sum(ph_all.values()), 1e-30) for k, v in ph_all.items()}
     roofline = dict(rooflines.get("update_fp64", rooflines.get("spmm_fp32", {})))
     roofline["phase_share"] = share

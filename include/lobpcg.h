@@ -121,6 +121,9 @@ typedef struct {
                                  0 (default): double-float in the FP64 refinement of the MIXED
                                  form, FP64 fused multiply-adds in the FP64 form; 1: double-float
                                  in every FP64 phase; -1: FP64 fused multiply-adds everywhere */
+  int tc_gram;                /* FP32 Gram matrices of the MIXED form: non-zero (default) on the
+                                 tcgen05 tensor cores (lobpcg_gram_f32_tcgen05), 0 with warp-level
+                                 mma.sync (lobpcg_gram_f32); both 3xTF32 */
 } lobpcg_options;
 
 typedef struct {
@@ -155,6 +158,8 @@ typedef struct {
   int skipped_recheck;          /* Algorithm 2 re-check Grams skipped (ortho_trim) */
   int skipped_test;             /* Algorithm 3 test Grams skipped (ortho_trim) */
   int df_products;              /* 1 if the FP64 Grams and updates ran in double-float arithmetic */
+  double rr_gram32_bytes;       /* algorithmic bytes of the FP32 Rayleigh-Ritz Grams (2 n s 4 each) */
+  int64_t rr_gram32_count;      /* their number */
 } lobpcg_info;
 
 /* Fills *opt with the defaults listed above.  Returns LOBPCG_EINVAL if opt is NULL. */
@@ -296,7 +301,8 @@ LOBPCG_API lobpcg_status lobpcg_update_f32(int64_t n, int nseg, const float* con
                                           const double* lam, double* resnorm, lobpcg_stream stream);
 
 /* C = X^T Y for FP32 blocks, the Gram of the mixed form (Algorithm 1's projected matrices
- * with FP32 storage).  X: n x p float (ldx), Y: n x q float (ldy), p, q <= 96.  C: device,
+ * with FP32 storage), with warp-level mma.sync (the solver's default is the tcgen05 kernel
+ * of lobpcg_gram_f32_tcgen05, see lobpcg_options.tc_gram).  X: n x p float (ldx), Y: n x q float (ldy), p, q <= 96.  C: device,
  * FP64, column-major p x q.  When the rows are 16-byte aligned with ldx == ldy a multiple
  * of 4, it runs on the tensor cores: TF32 mma with the 3xTF32 split, x = x_hi + x_lo and
  * a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi, which keeps ~21 bits per product.  Otherwise it
@@ -304,6 +310,19 @@ LOBPCG_API lobpcg_status lobpcg_update_f32(int64_t n, int nseg, const float* con
  * order). */
 LOBPCG_API lobpcg_status lobpcg_gram_f32(int64_t n, int p, const float* X, int ldx, int q, const float* Y,
                               int ldy, double* C, lobpcg_stream stream);
+
+/* The FP32 Gram of lobpcg_gram_f32 (3xTF32 products, FP32 sums within a CTA, FP64 across
+ * CTAs) on the 5th-generation tensor cores: rows staged by TMA bulk copies, operands split
+ * into TF32 hi / lo parts in shared memory, tcgen05.mma with the accumulator in tensor
+ * memory, each 32- or 64-row chunk's sum added to FP32 running sums with round-to-nearest
+ * adds.  X, Y: 16-byte aligned, one row stride (ldx == ldy, a multiple of 4); p, q <= 96.
+ * Each copy reads the rows' full stride except for the last row, of which it reads the
+ * used columns rounded up to 16 bytes (never past the 16-byte granule of the last
+ * element).  EINVAL for other layouts; ECUDA if a CTA gave up waiting on a copy, an MMA
+ * or a pipeline stage.  The operation is Algorithm 1's Gram; the kernel design is not
+ * from the paper. */
+LOBPCG_API lobpcg_status lobpcg_gram_f32_tcgen05(int64_t n, int p, const float* X, int ldx, int q, const float* Y,
+                                                 int ldy, double* C, lobpcg_stream stream);
 
 /* Symmetric eigen-decomposition of s x s column-major a (s <= 96) by parallel-order
  * Jacobi rotations in FP64 (the Rayleigh-Ritz solve of Algorithm 1).  lam: device, s

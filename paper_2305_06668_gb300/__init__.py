@@ -42,7 +42,7 @@ class _Options(C.Structure):
                 ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
                 ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
                 ("mixed_switch", C.c_double), ("autotune", C.c_int), ("ortho_trim", C.c_int),
-                ("df_products", C.c_int)]
+                ("df_products", C.c_int), ("tc_gram", C.c_int)]
 
 
 class _Info(C.Structure):
@@ -56,7 +56,8 @@ class _Info(C.Structure):
                 ("update_fp64_flops", C.c_double), ("update_fp64_launches", C.c_int64),
                 ("spmm_variant_fp32", C.c_int), ("spmm_variant_fp64", C.c_int), ("w_dropped", C.c_int),
                 ("p_dropped", C.c_int), ("ortho_grams", C.c_int), ("skipped_recheck", C.c_int),
-                ("skipped_test", C.c_int), ("df_products", C.c_int)]
+                ("skipped_test", C.c_int), ("df_products", C.c_int), ("rr_gram32_bytes", C.c_double),
+                ("rr_gram32_count", C.c_int64)]
 
 
 def library_path() -> pathlib.Path:
@@ -77,7 +78,7 @@ def lib():
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
                      "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32",
                      "lobpcg_probe_fma_rate", "lobpcg_gram_f64_df", "lobpcg_update_f64_df",
-                     "lobpcg_spmm_csr_f64_df"):
+                     "lobpcg_spmm_csr_f64_df", "lobpcg_gram_f32_tcgen05"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -147,7 +148,7 @@ class Solver:
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
                  mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
-                 ortho_trim: bool = True, df_products: int = 0, mass=None, stream=None):
+                 ortho_trim: bool = True, df_products: int = 0, tc_gram: bool = True, mass=None, stream=None):
         torch = _torch()
         L = lib()
         self._keep = [diag, row_ptr, col_idx, val, dense, mass]
@@ -175,6 +176,7 @@ class Solver:
         o.autotune = 1 if autotune else 0
         o.ortho_trim = 1 if ortho_trim else 0
         o.df_products = int(df_products)
+        o.tc_gram = 1 if tc_gram else 0
         w = None
         if mlp_weights is not None:
             w = np.ascontiguousarray(mlp_weights, dtype=np.float32)
@@ -354,6 +356,18 @@ def spmm_csr_df(row_ptr, col_idx, val, X, Y=None, stream=None):
                                         C.c_int64(val.numel()), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), _ptr(Y),
                                         C.c_int(Y.stride(0)), _stream(stream)))
     return Y
+
+
+def gram_f32_tcgen05(X, Y, stream=None):
+    """C = X^T Y of FP32 row-major CUDA blocks (one aligned row stride) on the tcgen05 tensor
+    cores (3xTF32), FP64 result."""
+    torch = _torch()
+    n, p = X.shape
+    q = Y.shape[1]
+    Cm = torch.empty((q, p), dtype=torch.float64, device=X.device)
+    _check(lib().lobpcg_gram_f32_tcgen05(C.c_int64(n), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), C.c_int(q),
+                                         _ptr(Y), C.c_int(Y.stride(0)), _ptr(Cm), _stream(stream)))
+    return Cm.t()
 
 
 def gram_df(X, Y, stream=None):

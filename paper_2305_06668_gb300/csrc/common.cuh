@@ -135,6 +135,13 @@ struct UpdateJob;
 template <class T>
 int launch_update_pipe(int64_t n, const UpdateJob<T>& job, const double* U, int s, int q, double alpha,
                        const double* lam, double* norm_part, int max_ctas, cudaStream_t st);
+// FP32 Gram partials on the 5th-generation tensor cores (tcgen05, TMA bulk copies, TMEM
+// accumulator; 3xTF32 products); returns 0 without launching when the operands do not
+// share one 16-byte aligned row stride or are wider than 96 columns.  umma_check reads and
+// clears its give-up flag (synchronising the stream) and throws if a CTA gave up waiting.
+int gram_partials_umma(int64_t n, const Cols<float>& a, const Cols<float>& b, bool upper, double* part,
+                       int max_ctas, cudaStream_t st);
+void umma_check(cudaStream_t st);
 // out[e] = sum_g part[g][e] for e < count (FP64, fixed order).
 void reduce_partials(const double* part, int nparts, int count, double* out, cudaStream_t st);
 

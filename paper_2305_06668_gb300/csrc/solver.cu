@@ -94,6 +94,8 @@ struct Stats {
   int p_dropped = 0;
   int ortho_grams = 0, skipped_recheck = 0, skipped_test = 0;
   int64_t b_products = 0;
+  double rr_gram32_bytes = 0.0;  // algorithmic bytes of the FP32 Rayleigh-Ritz Grams (V and AV read once)
+  int64_t rr_gram32_count = 0;
 };
 
 // Optional per-phase timing with CUDA events recorded on the solver stream.
@@ -445,8 +447,13 @@ template <class T>
 void gram(lobpcg_ctx& c, const Cols<T>& a, const Cols<T>& b, bool upper, double* out) {
   const int pa = a.width(), pb = b.width();
   int parts = 0;
-  if constexpr (std::is_same<T, double>::value)
+  if constexpr (std::is_same<T, double>::value) {
     if (c.df_on) parts = gram_partials_df(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
+  } else {
+    // FP32: the tcgen05 kernel when the blocks fit it (every block the solver allocates);
+    // its give-up flag is checked once per solve (umma_check)
+    if (c.opt.tc_gram != 0) parts = gram_partials_umma(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
+  }
   if (!parts) parts = gram_partials<T>(c.A.n, a, b, upper, c.Gpart, c.max_ctas, c.st);
   reduce_partials(c.Gpart, parts, pa * pb, out, c.st);
 }
@@ -717,6 +724,7 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     }
     c.prof.mark(PH_RR_GRAM);
     gram<T>(c, V, AV, true, c.G);                                       // a = V^T AV (upper)
+    if (sizeof(T) == 4) c.stats.rr_gram32_bytes += 2.0 * (double)n * s * sizeof(T), c.stats.rr_gram32_count++;
     c.prof.mark(PH_RR_EIG);
     // Rayleigh-Ritz; the FP32 phase, whose Ritz vectors go to FP32 blocks (rounding 6e-8),
     // takes the two-stage solver stopped at 1e-10 relative, the FP64 phase plain FP64 Jacobi
@@ -1036,6 +1044,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->autotune = 0;
   opt->ortho_trim = 1;
   opt->df_products = 0;
+  opt->tc_gram = 1;
   return LOBPCG_OK;
 }
 
@@ -1286,6 +1295,7 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
     LB_CUDA(cudaMemcpyAsync(resnorms, c->resnorm, k * sizeof(double), cudaMemcpyDeviceToHost, c->st));
     LB_CUDA(cudaEventRecord(e1, c->st));
     c->sync();
+    if (c->opt.precision == LOBPCG_MIXED) umma_check(c->st);
     float ms = 0.f;
     LB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
@@ -1322,6 +1332,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       info->skipped_recheck = c->stats.skipped_recheck;
       info->skipped_test = c->stats.skipped_test;
       info->df_products = (c->opt.precision == LOBPCG_MIXED) ? (c->opt.df_products >= 0) : (c->opt.df_products > 0);
+      info->rr_gram32_bytes = c->stats.rr_gram32_bytes;
+      info->rr_gram32_count = c->stats.rr_gram32_count;
     }
     for (int j = 0; j < k; ++j)
       if (!std::isfinite(evals[j]) || !std::isfinite(resnorms[j]))
@@ -1536,8 +1548,28 @@ extern "C" lobpcg_status lobpcg_gram_f32(int64_t n, int p, const float* X, int l
     require(p >= 1 && q >= 1 && p <= kMaxS && q <= kMaxS && ldx >= p && ldy >= q,
             "lobpcg_gram_f32: need 1 <= p, q <= 96, ld >= width");
     ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    s.c.opt.tc_gram = 0;  // the warp-level kernel; lobpcg_gram_f32_tcgen05 is the tcgen05 one
     gram<float>(s.c, cols1<float>(X, ldx, p), cols1<float>(Y, ldy, q), false, C);
     s.c.sync();
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_gram_f32_tcgen05(int64_t n, int p, const float* X, int ldx, int q, const float* Y,
+                                                 int ldy, double* C, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && X && Y && C, "lobpcg_gram_f32_tcgen05: NULL argument or n < 1");
+    require(p >= 1 && q >= 1 && p <= kMaxS && q <= kMaxS && ldx >= p && ldy >= q,
+            "lobpcg_gram_f32_tcgen05: need 1 <= p, q <= 96, ld >= width");
+    require(ldx == ldy && ldx % 4 == 0 && !(reinterpret_cast<uintptr_t>(X) & 15) &&
+                !(reinterpret_cast<uintptr_t>(Y) & 15),
+            "lobpcg_gram_f32_tcgen05: X and Y must be 16-byte aligned with one row stride, a multiple of 4");
+    ScratchCtx s(n, reinterpret_cast<cudaStream_t>(stream));
+    const int parts = gram_partials_umma(n, cols1<float>(X, ldx, p), cols1<float>(Y, ldy, q), false, s.c.Gpart,
+                                         s.c.max_ctas, s.c.st);
+    if (!parts) throw InvalidArg("lobpcg_gram_f32_tcgen05: operands do not fit the kernel");
+    reduce_partials(s.c.Gpart, parts, p * q, C, s.c.st);
+    umma_check(s.c.st);
     return LOBPCG_OK;
   });
 }
