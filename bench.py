@@ -532,6 +532,45 @@ def run_small_config(args):
     return 0
 
 
+def run_gram_config(args):
+    """Side line: the FP32 Gram C = X^T Y at n = 2*10^6 rows, tcgen05 kernel against the
+    warp-level mma.sync kernel, on the Gram shapes of the headline solve (63 x 63 and 42 x 21
+    over two blocks, X^T X over 21 columns) and the widest block (96 x 96).  Each call is timed
+    with CUDA events around the C-ABI call, which includes its scratch set-up; the kernels'
+    own times come from an ncu launch list of this command."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_06668_gb300 as lb
+    n = N_ROWS
+    g = torch.Generator(device="cuda").manual_seed(SEED)
+    shapes = [("63x63", 63, 63, 64, False), ("42x21", 42, 21, 44, False), ("21x21_same", 21, 21, 24, True),
+              ("96x96", 96, 96, 96, False)]
+    out = {}
+    for name, p, q, ld, same in shapes:
+        X = torch.randn(n, ld, device="cuda", generator=g)[:, :p]
+        Y = X[:, :q] if same else torch.randn(n, ld, device="cuda", generator=g)[:, :q]
+        nbytes = n * (p + (0 if same else q)) * 4
+        row = {}
+        for kname, fn in (("tcgen05", lb.gram_f32_tcgen05), ("mma_sync", lb.gram_f32)):
+            for _ in range(args.warmup):
+                fn(X, Y)
+            ts = []
+            for _ in range(max(1, args.steps)):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn(X, Y)
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1) * 1e-3)
+            row[kname] = {"call_seconds": float(np.median(ts))}
+        row["bytes"] = nbytes
+        out[name] = row
+        del X, Y
+    print(json.dumps({"side_line": "fp32 gram kernels", "n": n, "shapes": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -540,9 +579,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense"],
+    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense", "gram"],
                     help="ci2m: the headline workload; batched: the 256-problem serving workload; "
-                         "cfg1 / dense: the n=4096 sparse and n=8192 dense configurations (side lines)")
+                         "cfg1 / dense: the n=4096 sparse and n=8192 dense configurations (side lines); "
+                         "gram: the FP32 Gram kernels at n=2e6 (side line)")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
@@ -556,6 +596,8 @@ def main():
         return run_batched(args)
     if args.config in ("cfg1", "dense"):
         return run_small_config(args)
+    if args.config == "gram":
+        return run_gram_config(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -341,6 +341,150 @@ __global__ void __launch_bounds__(256, 3) update_df_kernel(int64_t n, UpdateJob<
   }
 }
 
+// 16-byte cp.async global -> shared; zero-filled (nothing read) when !valid
+__device__ __forceinline__ void cp_async16_df(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0));
+}
+
+// update_df_kernel with the next slab of rows in flight while the current one is computed.
+// Slab rows (FP64, each segment padded to an even width so every row piece is whole 16-byte
+// units) go to `raw` by cp.async; they are split into float pairs (sIn) once they land, and
+// the copies of the following slab start as soon as raw is free, so the global-load latency
+// overlaps the double-float products.  R = rows per slab = rows of one thread pass, so every
+// thread has a row.  Needs 16-byte aligned segments and even row strides (checked by the
+// launcher).  Arithmetic, order of the products and the FP64 epilogue as in update_df_kernel.
+template <int CJ>
+__global__ void __launch_bounds__(256, 2) update_df_async_kernel(int64_t n, UpdateJob<double> job,
+                                                              const double* __restrict__ U, int s, int q,
+                                                              double alpha, const double* __restrict__ lam,
+                                                              double* __restrict__ norm_part, int64_t rows_per_cta,
+                                                              int R, int sraw) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int qpad = (q + CJ - 1) / CJ * CJ;
+  const int nprod = job.nprod;
+  float2* sU = reinterpret_cast<float2*>(smem_raw);    // s x qpad, row-major: alpha U split
+  float2* sIn = sU + s * qpad;                         // nprod x R x s
+  double* raw = reinterpret_cast<double*>(sIn + (nprod * R * s + 1) / 2 * 2);  // nprod x R x sraw, 16-byte aligned
+  // column l -> offset in a raw row, past the raw slab (or the norm partials if larger)
+  int* lraw = reinterpret_cast<int*>(raw + max(nprod * R * sraw, norm_part ? R * 2 * qpad : 0));
+  const bool unit = job.unit_base != 0;
+  for (int e = threadIdx.x; e < s * qpad; e += blockDim.x) {
+    const int l = e / qpad, j = e % qpad;
+    sU[e] = j < q ? df_split(alpha * U[l + j * s] - (unit && l == j ? 1.0 : 0.0)) : make_float2(0.f, 0.f);
+  }
+  if (threadIdx.x == 0) {
+    int l = 0, roff = 0;
+    for (int g = 0; g < job.in[0].nseg; ++g) {
+      const int w = job.in[0].w[g];
+      for (int j = 0; j < w; ++j) lraw[l++] = roff + j;
+      roff += w + (w & 1);
+    }
+  }
+  const int tpr = qpad / CJ;
+  const int rows_per_pass = blockDim.x / tpr;
+  const int rr = threadIdx.x / tpr, cj = threadIdx.x % tpr;
+  const bool active = rr < rows_per_pass && rr < R;
+  double nsum[CJ], nmax[CJ];
+#pragma unroll
+  for (int j = 0; j < CJ; ++j) nsum[j] = 0.0, nmax[j] = 0.0;
+
+  const int64_t r_begin = (int64_t)blockIdx.x * rows_per_cta;
+  const int64_t r_end = min(n, r_begin + rows_per_cta);
+  auto issue = [&](int64_t r0) {
+    for (int t = 0; t < nprod; ++t) {
+      const Cols<double>& c = job.in[t];
+      int roff = 0;
+      for (int g = 0; g < c.nseg; ++g) {
+        const int w = c.w[g], units = (w + 1) / 2, ld = c.ld[g];
+        const double* p = c.p[g];
+        for (int e = threadIdx.x; e < R * units; e += blockDim.x) {
+          const int r = e / units, u = e - r * units;
+          const int64_t row = r0 + r;
+          const bool ok = row < r_end;
+          cp_async16_df(raw + (t * R + r) * sraw + roff + 2 * u, p + (ok ? row : r0) * ld + 2 * u, ok);
+        }
+        roff += 2 * units;
+      }
+    }
+    asm volatile("cp.async.commit_group;\n" ::);
+  };
+  if (r_begin < r_end) issue(r_begin);
+  for (int64_t r0 = r_begin; r0 < r_end; r0 += R) {
+    asm volatile("cp.async.wait_group 0;\n" ::);
+    __syncthreads();  // the slab landed (every thread's copies) and the previous slab is consumed
+    for (int t = 0; t < nprod; ++t)
+      for (int e = threadIdx.x; e < R * s; e += blockDim.x) {
+        const int r = e / s, l = e - r * s;
+        sIn[(t * R + r) * s + l] = r0 + r < r_end ? df_split(raw[(t * R + r) * sraw + lraw[l]]) : make_float2(0.f, 0.f);
+      }
+    __syncthreads();  // raw is free: the next slab's copies overlap this slab's products
+    if (r0 + R < r_end) issue(r0 + R);
+    if (!active) continue;
+    const int r = rr;
+    const int64_t row = r0 + r;
+    if (row >= r_end) continue;
+    double res[2][CJ];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      if (t >= nprod) break;
+      DfAcc acc[CJ];
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) df_zero(acc[j]);
+      const float2* x = sIn + (t * R + r) * s;
+      for (int l = 0; l < s; ++l) {
+        const float2 xv = x[l];
+#pragma unroll
+        for (int j = 0; j < CJ; ++j) df_fma(acc[j], xv, sU[l * qpad + cj * CJ + j]);
+      }
+      double* o = job.out[t] + row * job.ld_out[t];
+      // the base is added in FP64 (one add per output), as in update_df_kernel
+      const double* b = unit ? job.in[0].p[0] + row * job.in[0].ld[0]
+                             : (job.base[t] ? job.base[t] + row * job.ld_base[t] : nullptr);
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        const int col = cj * CJ + j;
+        double v = df_value(acc[j]);
+        if (b && col < q) v = b[col] + v;
+        res[t][j] = v;
+        if (col < q) o[col] = v;
+      }
+    }
+    if (norm_part) {
+#pragma unroll
+      for (int j = 0; j < CJ; ++j) {
+        const int col = cj * CJ + j;
+        if (col < q) {
+          const double rij = fma(-lam[col], res[0][j], res[1][j]);  // AX - lam X, one rounding
+          nsum[j] = fma(rij, rij, nsum[j]);
+          nmax[j] = fmax(nmax[j], fabs(rij));
+        }
+      }
+    }
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+  if (!norm_part) return;
+  __syncthreads();
+  double* sNorm = raw;  // [rows_per_pass][2 * qpad], in the idle slab buffer
+  if (active) {
+#pragma unroll
+    for (int j = 0; j < CJ; ++j) {
+      sNorm[rr * 2 * qpad + cj * CJ + j] = nsum[j];
+      sNorm[rr * 2 * qpad + qpad + cj * CJ + j] = nmax[j];
+    }
+  }
+  __syncthreads();
+  for (int col = threadIdx.x; col < q; col += blockDim.x) {
+    double s2 = 0.0, mx = 0.0;
+    for (int g = 0; g < min(rows_per_pass, R); ++g) {
+      s2 += sNorm[g * 2 * qpad + col];
+      mx = fmax(mx, sNorm[g * 2 * qpad + qpad + col]);
+    }
+    norm_part[(int64_t)blockIdx.x * 2 * q + col] = s2;
+    norm_part[(int64_t)blockIdx.x * 2 * q + q + col] = mx;
+  }
+}
+
 template <class T>
 __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __restrict__ AX, int ld,
                                const double* __restrict__ lam, int c0, int a,
@@ -520,9 +664,54 @@ int launch_update(int64_t n, const UpdateJob<T>& job, const double* U, int s, in
   return (int)ctas;
 }
 
+// The asynchronous-staging form of the double-float update when the layout allows it
+// (segments 16-byte aligned, even row strides); 0 otherwise.
+int launch_update_df_async(int64_t n, const UpdateJob<double>& job, const double* U, int s, int q, double alpha,
+                           const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
+  constexpr int CJ = 4;
+  int sraw = 0;
+  for (int t = 0; t < job.nprod; ++t) {
+    int sr = 0;
+    for (int g = 0; g < job.in[t].nseg; ++g) {
+      if ((reinterpret_cast<uintptr_t>(job.in[t].p[g]) & 15) || (job.in[t].ld[g] & 1)) return 0;
+      sr += job.in[t].w[g] + (job.in[t].w[g] & 1);
+      if (t > 0 && job.in[t].w[g] != job.in[0].w[g]) return 0;
+    }
+    if (t > 0 && job.in[t].nseg != job.in[0].nseg) return 0;
+    sraw = sr;
+  }
+  const int qpad = round_up(q, CJ);
+  const int threads = 256;
+  const int tpr = qpad / CJ;
+  const int R = threads / tpr;  // one row per thread pass
+  const size_t in_bytes = (size_t)(job.nprod * R * s + 1) / 2 * 2 * sizeof(float2);
+  const size_t raw_bytes = (size_t)job.nprod * R * sraw * sizeof(double);
+  const size_t norm = norm_part ? (size_t)R * 2 * qpad * sizeof(double) : 0;
+  // sU, sIn, then raw (reused for the norm partials at the end), then the column table
+  const size_t smem = (size_t)s * qpad * sizeof(float2) + in_bytes + std::max(raw_bytes, norm) +
+                      (size_t)kMaxS * sizeof(int) + 16;
+  if (smem > 110 * 1024) return 0;  // two CTAs per SM
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(update_df_async_kernel<CJ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 110 * 1024));
+    return true;
+  }();
+  (void)attr;
+  const int64_t max_df = std::max<int64_t>(max_ctas, 2 * (int64_t)num_sms());
+  int64_t ctas = std::min<int64_t>(max_df, ceil_div(n, R));
+  if (ctas < 1) ctas = 1;
+  const int64_t rpc = (ceil_div(n, ctas) + R - 1) / R * R;
+  ctas = std::max<int64_t>(1, ceil_div(n, rpc));
+  update_df_async_kernel<CJ><<<(unsigned)ctas, threads, smem, st>>>(n, job, U, s, q, alpha, lam, norm_part, rpc, R,
+                                                                    sraw);
+  LB_LAUNCH_CHECK();
+  return (int)ctas;
+}
+
 int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, int s, int q, double alpha,
                      const double* lam, double* norm_part, int max_ctas, cudaStream_t st) {
   if (q <= 0 || n <= 0) return 0;
+  if (const int parts = launch_update_df_async(n, job, U, s, q, alpha, lam, norm_part, max_ctas, st)) return parts;
   constexpr int CJ = 4, R = 32;
   const int qpad = round_up(q, CJ);
   const int threads = 256;

@@ -70,17 +70,23 @@ def test_gram_df_exact_on_small_integers():
     assert np.array_equal(got, exact)
 
 
-@pytest.mark.parametrize("mode", ["pair_norm", "base_inplace", "right_inplace", "plain"])
+@pytest.mark.parametrize("mode", ["pair_norm", "base_inplace", "right_inplace", "plain", "plain_odd_ld",
+                                  "pair_norm_ragged"])
 def test_update_f64_df_matches_oracle(mode):
     """X = base + alpha [V_g] U in double-float against the oracle's FP64 product (V U as a
-    Gram of V^T and U over the s rows), to 2^-44 (|V| |U|) (+ |base|)."""
+    Gram of V^T and U over the s rows), to (8 + s + 1) 2^-47 (|V| |U|) (+ |base|).  Even row
+    strides take the kernel that stages the next slab asynchronously; an odd stride
+    (plain_odd_ld) takes the synchronous one; ragged segment widths and a row count that is
+    not a multiple of the slab exercise the padding and the last slab."""
     torch = cuda()
     import paper_2305_06668_gb300 as lb
     n, ws, q = 90_001, [21, 21, 21], 21
     if mode == "right_inplace":
         ws, q = [21], 21
+    if mode == "pair_norm_ragged":
+        n, ws, q = 77_777, [7, 22, 13], 9
     s = sum(ws)
-    ld = 24
+    ld = 23 if mode == "plain_odd_ld" else 24
     Vs = [synth.gaussian_block(n, w, seed=500 + i) for i, w in enumerate(ws)]
     AVs = [synth.gaussian_block(n, w, seed=600 + i) for i, w in enumerate(ws)]
     U = synth.gaussian_block(s, q, seed=17) / np.sqrt(s)
@@ -91,7 +97,7 @@ def test_update_f64_df_matches_oracle(mode):
     ref = oracle.gram(Vcat.T.copy(), U)
     BOUND = bound(s + 1)  # s products and the base
     tol = BOUND * (np.abs(Vcat) @ np.abs(U)) + 1e-300
-    if mode == "pair_norm":
+    if mode.startswith("pair_norm"):
         lam = np.linspace(-1.0, 2.0, q)
         X, AX, rn = lb.update_f64_df(Vd, Ud, AV=AVd, lam=torch.from_numpy(lam).cuda(), resnorm=True)
         Xh, AXh = X.cpu().numpy(), AX.cpu().numpy()
