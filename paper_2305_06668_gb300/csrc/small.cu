@@ -36,19 +36,47 @@ __device__ double block_max(double v, double* red) {
   return s;
 }
 
+// Pairs of one parallel-order round (circle method, player N-1 fixed): pair i of round r
+// is (p, q) with p < q; q may be the dummy player s when s is odd.
+__device__ __forceinline__ void round_pair(int N, int r, int i, int& p, int& q) {
+  if (i == 0) p = N - 1, q = r;
+  else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
+  if (p > q) { const int t = p; p = q; q = t; }
+}
+
+// Pair blocks of a round: item e -> (i1, i2), i1 <= i2, the upper triangle of the
+// half x half grid of pair blocks in row-major order, as i1 << 8 | i2 (table filled once
+// per call; half <= 48).
+constexpr int kMaxBlk = (kMaxS / 2) * (kMaxS / 2 + 1) / 2;
+__shared__ unsigned short g_blk[kMaxBlk];  // one per CTA, shared by the Jacobi routines of a kernel
+__device__ void fill_blocks(int half, unsigned short* blk) {
+  for (int i1 = threadIdx.x; i1 < half; i1 += blockDim.x) {
+    const int base = i1 * half - i1 * (i1 - 1) / 2;  // items of the rows before i1
+    for (int i2 = i1; i2 < half; ++i2) blk[base + i2 - i1] = (unsigned short)(i1 << 8 | i2);
+  }
+  __syncthreads();
+}
+
 // Parallel-order (round-robin) cyclic Jacobi on the symmetric s x s matrix a (column-
 // major, leading dimension lda, overwritten by its rotated form) accumulating the
 // rotations in V (s x s, ldv; set to the identity first when init_v).  Each round applies
 // s/2 disjoint rotations (classical smaller-angle rotation of Golub & Van Loan, Sec. 8.5)
-// as J^T A then A J, in the arithmetic of T.  Stops when off(a) <= rel_tol * ||a||_F.
-// Returns the number of sweeps, or -1 without convergence in max_sweeps.
+// as J^T A J, in the arithmetic of T.  A round is two phases: the rotation of every pair,
+// then one pass that maps every 2 x 2 block of a between two pairs (rows of pair i1,
+// columns of pair i2; the upper triangle of blocks, mirrored, so a stays exactly
+// symmetric) to R_i1^T a_blk R_i2, rows first then columns, with the pair's own
+// off-diagonal entry set to zero, together with columns p, q of V.  Stops when
+// off(a) <= rel_tol * ||a||_F.  Returns the number of sweeps, or -1 without convergence
+// in max_sweeps.
 template <class T>
 __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double* red, double rel_tol,
                              int max_sweeps, bool init_v) {
   const int N = s + (s & 1);
   const int half = N / 2;
-  // (pair, column) items of a round as e = pair * sp + column with sp = pow2 >= s, so that
-  // the round loops use shifts instead of divisions by s
+  const int nblk = half * (half + 1) / 2;
+  unsigned short* blk = g_blk;
+  fill_blocks(half, blk);
+  // (pair, row) items of V as e = pair * sp + row with sp = pow2 >= s (shifts, no division)
   const int sh = s <= 32 ? 5 : (s <= 64 ? 6 : 7), sp = 1 << sh;
   if (init_v)
     for (int e = threadIdx.x; e < s * s; e += blockDim.x) {
@@ -74,57 +102,63 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // phase A: rotation of every pair of this Jacobi round (circle method, player N-1 fixed)
+      // phase A: rotation of every pair of this round (identity for a dummy or zero pair)
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
-        if (i == 0) p = N - 1, q = r;
-        else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
-        if (p > q) { const int t = p; p = q; q = t; }
+        round_pair(N, r, i, p, q);
         T c = T(1), sn = T(0);
-        bool skip = q >= s;
-        if (!skip) {
+        bool rotate = false;
+        if (q < s) {
           const T apq = a[p + q * lda];
-          if (apq == T(0)) {
-            skip = true;
-          } else {
+          if (apq != T(0)) {
             const T tau = (a[q + q * lda] - a[p + p * lda]) / (T(2) * apq);
             const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
             c = T(1) / sqrt(T(1) + t * t);
             sn = t * c;
+            rotate = true;
           }
         }
-        rot[4 * i + 0] = skip ? T(-1) : (T)p;
-        rot[4 * i + 1] = (T)q;
+        rot[4 * i + 0] = (T)(p * 256 + q);
+        rot[4 * i + 1] = rotate ? T(1) : T(0);
         rot[4 * i + 2] = c;
         rot[4 * i + 3] = sn;
       }
       __syncthreads();
-      // phase B: rows p, q of a (J^T A) and columns p, q of V (V J)
-      for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
-        const int i = e >> sh, j = e & (sp - 1);
-        if (j >= s || rot[4 * i] < T(0)) continue;
-        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
-        const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
-        const T apj = a[p + j * lda], aqj = a[q + j * lda];
-        a[p + j * lda] = c * apj - sn * aqj;
-        a[q + j * lda] = sn * apj + c * aqj;
-        const T vjp = V[j + p * ldv], vjq = V[j + q * ldv];
-        V[j + p * ldv] = c * vjp - sn * vjq;
-        V[j + q * ldv] = sn * vjp + c * vjq;
-      }
-      __syncthreads();
-      // phase C: columns p, q of a (A J); the annihilated pair is set to exactly zero
-      for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
-        const int i = e >> sh, j = e & (sp - 1);
-        if (j >= s || rot[4 * i] < T(0)) continue;
-        const int p = (int)rot[4 * i], q = (int)rot[4 * i + 1];
-        const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
-        const T ajp = a[j + p * lda], ajq = a[j + q * lda];
-        T np = c * ajp - sn * ajq, nq = sn * ajp + c * ajq;
-        if (j == p) nq = T(0);
-        if (j == q) np = T(0);
-        a[j + p * lda] = np;
-        a[j + q * lda] = nq;
+      // phase B: the blocks of a, then columns p, q of V (V J)
+      for (int e = threadIdx.x; e < nblk + (half << sh); e += blockDim.x) {
+        if (e < nblk) {
+          const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
+          if (rot[4 * i1 + 1] == T(0) && rot[4 * i2 + 1] == T(0)) continue;  // both identity
+          const int pq1 = (int)rot[4 * i1], p1 = pq1 >> 8, q1 = pq1 & 255;
+          const int pq2 = (int)rot[4 * i2], p2 = pq2 >> 8, q2 = pq2 & 255;
+          const T c1 = rot[4 * i1 + 2], s1 = rot[4 * i1 + 3], c2 = rot[4 * i2 + 2], s2 = rot[4 * i2 + 3];
+          const bool v1 = q1 < s, v2 = q2 < s;
+          const T x00 = a[p1 + p2 * lda], x01 = v2 ? a[p1 + q2 * lda] : T(0);
+          const T x10 = v1 ? a[q1 + p2 * lda] : T(0), x11 = v1 && v2 ? a[q1 + q2 * lda] : T(0);
+          // rows (J_1^T), then columns (J_2)
+          const T r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+          const T r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+          T n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
+          T n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
+          if (i1 == i2) {  // the pair's own block: its off-diagonal entry is annihilated
+            if (rot[4 * i1 + 1] != T(0)) n01 = n10 = T(0);
+            a[p1 + p1 * lda] = n00;
+            if (v1) a[q1 + q1 * lda] = n11, a[p1 + q1 * lda] = n01, a[q1 + p1 * lda] = n10;
+            continue;
+          }
+          a[p1 + p2 * lda] = n00, a[p2 + p1 * lda] = n00;
+          if (v2) a[p1 + q2 * lda] = n01, a[q2 + p1 * lda] = n01;
+          if (v1) a[q1 + p2 * lda] = n10, a[p2 + q1 * lda] = n10;
+          if (v1 && v2) a[q1 + q2 * lda] = n11, a[q2 + q1 * lda] = n11;
+        } else {
+          const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
+          if (j >= s || rot[4 * i + 1] == T(0)) continue;
+          const int pq = (int)rot[4 * i], p = pq >> 8, q = pq & 255;
+          const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
+          const T vjp = V[j + p * ldv], vjq = V[j + q * ldv];
+          V[j + p * ldv] = c * vjp - sn * vjq;
+          V[j + q * ldv] = sn * vjp + c * vjq;
+        }
       }
       __syncthreads();
     }
@@ -137,11 +171,16 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
 // FP32 adds errors of order 6e-8 |E| there.  The diagonal d, the rotation parameters and
 // Dl = V - I (ld ldd), the rotation product accumulated so far, stay in FP64.  Dl must be
 // FP64 because the angles inside a cluster of eigenvalues are not small.  Dl must hold
-// zeros on entry.  Stops when off(E) <= rel_tol * fro.  Returns the sweeps done, or -1.
+// zeros on entry.  Rounds as in jacobi_sweeps: the pair rotations (with d updated), then
+// one pass over the 2 x 2 blocks of E between different pairs and columns p, q of Dl.
+// Stops when off(E) <= rel_tol * fro.  Returns the sweeps done, or -1.
 __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, int ldd, double* rot, double* red,
                              double rel_tol, double fro, int max_sweeps) {
   const int N = s + (s & 1);
   const int half = N / 2;
+  const int nblk = half * (half + 1) / 2;
+  unsigned short* blk = g_blk;
+  fill_blocks(half, blk);
   const int sh = s <= 32 ? 5 : (s <= 64 ? 6 : 7), sp = 1 << sh;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double o2 = 0.0;
@@ -155,69 +194,70 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // rot[4i .. 4i+3] = 128 p + q (< 0: skip), c - 1, c, s; the diagonal is updated here
+      // rot[4i .. 4i+3] = 256 p + q, c - 1 (0: identity), c, s; the diagonal is updated here
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
-        if (i == 0) p = N - 1, q = r;
-        else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
-        if (p > q) { const int t = p; p = q; q = t; }
-        double c = 1.0, sn = 0.0;
-        bool skip = q >= s;
-        if (!skip) {
+        round_pair(N, r, i, p, q);
+        double c = 1.0, sn = 0.0, cm1 = 0.0;
+        bool rotate = false;
+        if (q < s) {
           const double apq = (double)E[p + q * lde];
-          if (apq == 0.0) {
-            skip = true;
-          } else {
+          if (apq != 0.0) {
             const double tau = (d[q] - d[p]) / (2.0 * apq);
             const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
             c = 1.0 / sqrt(1.0 + t * t);
             sn = t * c;
             d[p] -= t * apq;
             d[q] += t * apq;
+            cm1 = -sn * sn / (1.0 + c);  // c - 1 without cancellation, once per pair
+            rotate = true;
           }
         }
-        rot[4 * i + 0] = skip ? -1.0 : (double)(p * 128 + q);
-        rot[4 * i + 1] = -sn * sn / (1.0 + c);  // c - 1 without cancellation, once per pair
+        rot[4 * i + 0] = (double)(p * 256 + q) + (rotate ? 0.5 : 0.0);
+        rot[4 * i + 1] = cm1;
         rot[4 * i + 2] = c;
         rot[4 * i + 3] = sn;
       }
       __syncthreads();
-      // rows p, q of E (entries outside the pair's 2 x 2 block) and columns p, q of Dl
-      for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
-        const int i = e >> sh, j = e & (sp - 1);
-        if (j >= s || rot[4 * i] < 0.0) continue;
-        const int pq = (int)rot[4 * i], p = pq >> 7, q = pq & 127;
-        const double cd = rot[4 * i + 2], sd = rot[4 * i + 3];
-        const float c = (float)cd, sn = (float)sd;
-        if (j != p && j != q) {
-          const float epj = E[p + j * lde], eqj = E[q + j * lde];
-          E[p + j * lde] = c * epj - sn * eqj;
-          E[q + j * lde] = sn * epj + c * eqj;
+      for (int e = threadIdx.x; e < nblk + (half << sh); e += blockDim.x) {
+        if (e < nblk) {
+          const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
+          const double k1 = rot[4 * i1], k2 = rot[4 * i2];
+          const bool rot1 = k1 != floor(k1), rot2 = k2 != floor(k2);
+          if (!rot1 && !rot2) continue;
+          const int pq1 = (int)k1, p1 = pq1 >> 8, q1 = pq1 & 255;
+          if (i1 == i2) {  // the pair's own off-diagonal entry is annihilated (d done above)
+            E[p1 + q1 * lde] = 0.f, E[q1 + p1 * lde] = 0.f;
+            continue;
+          }
+          const int pq2 = (int)k2, p2 = pq2 >> 8, q2 = pq2 & 255;
+          const float c1 = (float)rot[4 * i1 + 2], s1 = (float)rot[4 * i1 + 3];
+          const float c2 = (float)rot[4 * i2 + 2], s2 = (float)rot[4 * i2 + 3];
+          const bool v1 = q1 < s, v2 = q2 < s;
+          const float x00 = E[p1 + p2 * lde], x01 = v2 ? E[p1 + q2 * lde] : 0.f;
+          const float x10 = v1 ? E[q1 + p2 * lde] : 0.f, x11 = v1 && v2 ? E[q1 + q2 * lde] : 0.f;
+          const float r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+          const float r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+          const float n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
+          const float n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
+          E[p1 + p2 * lde] = n00, E[p2 + p1 * lde] = n00;
+          if (v2) E[p1 + q2 * lde] = n01, E[q2 + p1 * lde] = n01;
+          if (v1) E[q1 + p2 * lde] = n10, E[p2 + q1 * lde] = n10;
+          if (v1 && v2) E[q1 + q2 * lde] = n11, E[q2 + q1 * lde] = n11;
+        } else {
+          // V' = V J with V = I + Dl
+          const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
+          const double k = rot[4 * i];
+          if (j >= s || k == floor(k)) continue;
+          const int pq = (int)k, p = pq >> 8, q = pq & 255;
+          const double cd = rot[4 * i + 2], sd = rot[4 * i + 3], cm1 = rot[4 * i + 1];
+          const double djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
+          double np = cd * djp - sd * djq, nq = sd * djp + cd * djq;
+          if (j == p) np += cm1, nq += sd;
+          if (j == q) np -= sd, nq += cm1;
+          Dl[j + p * ldd] = np;
+          Dl[j + q * ldd] = nq;
         }
-        // V' = V J with V = I + Dl
-        const double cm1 = rot[4 * i + 1];
-        const double djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
-        double np = cd * djp - sd * djq, nq = sd * djp + cd * djq;
-        if (j == p) np += cm1, nq += sd;
-        if (j == q) np -= sd, nq += cm1;
-        Dl[j + p * ldd] = np;
-        Dl[j + q * ldd] = nq;
-      }
-      __syncthreads();
-      // columns p, q of E; the pair's own off-diagonal entry is annihilated
-      for (int e = threadIdx.x; e < (half << sh); e += blockDim.x) {
-        const int i = e >> sh, j = e & (sp - 1);
-        if (j >= s || rot[4 * i] < 0.0) continue;
-        const int pq = (int)rot[4 * i], p = pq >> 7, q = pq & 127;
-        const float c = (float)rot[4 * i + 2], sn = (float)rot[4 * i + 3];
-        if (j == p || j == q) {
-          if (j == p) E[q + p * lde] = 0.f;
-          else E[p + q * lde] = 0.f;
-          continue;
-        }
-        const float ejp = E[j + p * lde], ejq = E[j + q * lde];
-        E[j + p * lde] = c * ejp - sn * ejq;
-        E[j + q * lde] = sn * ejp + c * ejq;
       }
       __syncthreads();
     }

@@ -691,6 +691,8 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   int pw = 0;  // width of P in the current basis
   double best_rk = 1e300, first_rk = -1.0;
   int since_best = 0;
+  double rk_hist[4] = {0.0, 0.0, 0.0, 0.0};  // the last four largest sought residuals
+  int nhist = 0;
   double lbest = 1e300;
   int lsince = 0;
 
@@ -759,16 +761,29 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
     if (stall_exit) {
       // mixed-precision switch: leave this precision once every one of the k sought
       // residuals is below switch_tol, or (switch_tol == 0) once the largest of them has
-      // reached its rounding floor: no 10% improvement for 2 iterations after it fell
-      // below 1% of its first value, or for 5 iterations at any level
+      // reached its rounding floor (reading R22): after it fell below 1% of its first
+      // value, either a sudden loss of a fast rate (over the three previous iterations it
+      // fell by a factor <= 0.6 per iteration on geometric average, this one cut it by
+      // less than 25%) or no 10% improvement for 2 iterations; at any level, no 10%
+      // improvement for 5 iterations
       double rk = 0.0;
       for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
       if (first_rk < 0.0) first_rk = rk;
+      bool rate_lost = false;
+      if (nhist >= 4 && rk <= 1e-2 * first_rk) {
+        const bool fast = rk_hist[3] <= 0.216 * rk_hist[0];  // (r3 / r0)^(1/3) <= 0.6
+        rate_lost = fast && rk > 0.75 * rk_hist[3];
+      }
+      if (nhist < 4) rk_hist[nhist++] = rk;
+      else rk_hist[0] = rk_hist[1], rk_hist[1] = rk_hist[2], rk_hist[2] = rk_hist[3], rk_hist[3] = rk;
       if (switch_tol > 0.0) {
         if (rk <= switch_tol) {
           cur = nxt;
           break;
         }
+      } else if (rate_lost) {
+        cur = nxt;
+        break;
       } else if (rk < 0.9 * best_rk) {
         best_rk = rk, since_best = 0;
       } else if (++since_best >= 5 || (since_best >= 2 && best_rk <= 1e-2 * first_rk)) {

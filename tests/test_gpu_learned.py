@@ -45,7 +45,10 @@ def test_learned_matches_oracle_eigenpairs(precision):
 
 
 def test_trained_network_cuts_iterations_on_heldout_ci_matrices():
-    """Held-out seeds of the CI-like family (not used in training)."""
+    """Held-out seeds of the CI-like family (not used in training).  The diagonal reference
+    gets a large iteration cap: its count is chaotic in the last bits of the arithmetic
+    (seed 2100 has taken 2,143 and 6,288 iterations on two builds whose Rayleigh-Ritz
+    eigensolvers differ only in rounding), while the learned form's is stable."""
     torch = cuda()
     import paper_2305_06668_gb300 as lb
     w = _weights()
@@ -55,7 +58,7 @@ def test_trained_network_cuts_iterations_on_heldout_ci_matrices():
         x0 = torch.from_numpy(synth.diag_guess(a.diag, 21, seed=seed, noise=0.0)).cuda()
         out = {}
         for name, kw in (("diag", {}), ("learned", dict(precond=lb.PREC_LEARNED, mlp_weights=w))):
-            s = lb.Solver(**t, extra=5, maxiter=4000, **kw)
+            s = lb.Solver(**t, extra=5, maxiter=20000 if name == "diag" else 4000, **kw)
             out[name] = s.solve(16, 1e-8, X0=x0)
             s.close()
         d, l = out["diag"], out["learned"]
