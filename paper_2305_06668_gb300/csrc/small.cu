@@ -39,8 +39,14 @@ __device__ double block_max(double v, double* red) {
 // Pairs of one parallel-order round (circle method, player N-1 fixed): pair i of round r
 // is (p, q) with p < q; q may be the dummy player s when s is odd.
 __device__ __forceinline__ void round_pair(int N, int r, int i, int& p, int& q) {
-  if (i == 0) p = N - 1, q = r;
-  else p = (r + i) % (N - 1), q = (r - i + (N - 1)) % (N - 1);
+  const int M = N - 1;  // r < M, 0 < i < N / 2: one correction brings r +- i into [0, M)
+  if (i == 0) {
+    p = M, q = r;
+  } else {
+    p = r + i, q = r - i;
+    if (p >= M) p -= M;
+    if (q < 0) q += M;
+  }
   if (p > q) { const int t = p; p = q; q = t; }
 }
 
@@ -76,6 +82,7 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
   const int nblk = half * (half + 1) / 2;
   unsigned short* blk = g_blk;
   fill_blocks(half, blk);
+  __shared__ int rpq[kMaxS / 2];
   // (pair, row) items of V as e = pair * sp + row with sp = pow2 >= s (shifts, no division)
   const int sh = s <= 32 ? 5 : (s <= 64 ? 6 : 7), sp = 1 << sh;
   if (init_v)
@@ -102,7 +109,8 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // phase A: rotation of every pair of this round (identity for a dummy or zero pair)
+      // phase A: rotation of every pair of this round (identity for a dummy or zero pair);
+      // rpq[i] = p << 8 | q, bit 16 set when the pair rotates
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
         round_pair(N, r, i, p, q);
@@ -118,30 +126,103 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
             rotate = true;
           }
         }
-        rot[4 * i + 0] = (T)(p * 256 + q);
-        rot[4 * i + 1] = rotate ? T(1) : T(0);
-        rot[4 * i + 2] = c;
-        rot[4 * i + 3] = sn;
+        rpq[i] = p << 8 | q | (rotate ? 1 << 16 : 0);
+        rot[2 * i + 0] = c;
+        rot[2 * i + 1] = sn;
       }
       __syncthreads();
-      // phase B: the blocks of a, then columns p, q of V (V J)
-      for (int e = threadIdx.x; e < nblk + (half << sh); e += blockDim.x) {
-        if (e < nblk) {
-          const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
-          if (rot[4 * i1 + 1] == T(0) && rot[4 * i2 + 1] == T(0)) continue;  // both identity
-          const int pq1 = (int)rot[4 * i1], p1 = pq1 >> 8, q1 = pq1 & 255;
-          const int pq2 = (int)rot[4 * i2], p2 = pq2 >> 8, q2 = pq2 & 255;
-          const T c1 = rot[4 * i1 + 2], s1 = rot[4 * i1 + 3], c2 = rot[4 * i2 + 2], s2 = rot[4 * i2 + 3];
+      // phase B: the blocks of a, then columns p, q of V (V J).  Items touch disjoint
+      // entries, so in FP64 a thread loads all of its (up to four) items before it stores
+      // any (the loads overlap the long FP64 latencies); in FP32 one item at a time is
+      // faster (measured at s = 63: 3.4k against 5.2k cycles per round)
+      const int total = nblk + (half << sh);
+      if constexpr (sizeof(T) == 4) {
+        for (int e = threadIdx.x; e < total; e += blockDim.x) {
+          if (e < nblk) {
+            const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
+            const int m1 = rpq[i1], m2 = rpq[i2];
+            if (!((m1 | m2) & (1 << 16))) continue;
+            const int p1 = (m1 >> 8) & 255, q1 = m1 & 255, p2 = (m2 >> 8) & 255, q2 = m2 & 255;
+            const T c1 = rot[2 * i1], s1 = rot[2 * i1 + 1], c2 = rot[2 * i2], s2 = rot[2 * i2 + 1];
+            const bool v1 = q1 < s, v2 = q2 < s;
+            const T x00 = a[p1 + p2 * lda], x01 = v2 ? a[p1 + q2 * lda] : T(0);
+            const T x10 = v1 ? a[q1 + p2 * lda] : T(0), x11 = v1 && v2 ? a[q1 + q2 * lda] : T(0);
+            const T r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
+            const T r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+            T n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
+            T n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
+            if (i1 == i2) {
+              n01 = n10 = T(0);
+              a[p1 + p1 * lda] = n00;
+              if (v1) a[q1 + q1 * lda] = n11, a[p1 + q1 * lda] = n01, a[q1 + p1 * lda] = n10;
+              continue;
+            }
+            a[p1 + p2 * lda] = n00, a[p2 + p1 * lda] = n00;
+            if (v2) a[p1 + q2 * lda] = n01, a[q2 + p1 * lda] = n01;
+            if (v1) a[q1 + p2 * lda] = n10, a[p2 + q1 * lda] = n10;
+            if (v1 && v2) a[q1 + q2 * lda] = n11, a[q2 + q1 * lda] = n11;
+          } else {
+            const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
+            const int m = rpq[i];
+            if (j >= s || !(m & (1 << 16))) continue;
+            const int p = (m >> 8) & 255, q = m & 255;
+            const T c = rot[2 * i], sn = rot[2 * i + 1];
+            const T vjp = V[j + p * ldv], vjq = V[j + q * ldv];
+            V[j + p * ldv] = c * vjp - sn * vjq;
+            V[j + q * ldv] = sn * vjp + c * vjq;
+          }
+        }
+      } else
+      for (int e0 = threadIdx.x; e0 < total; e0 += 4 * blockDim.x) {
+        int kind[4], m1[4], m2[4];
+        T x[4][4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = e0 + k * blockDim.x;
+          kind[k] = 0;
+          if (e < nblk) {
+            const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
+            m1[k] = rpq[i1], m2[k] = rpq[i2];
+            if (!((m1[k] | m2[k]) & (1 << 16))) continue;  // both identity
+            kind[k] = 1 + (i1 == i2);
+            const int p1 = (m1[k] >> 8) & 255, q1 = m1[k] & 255, p2 = (m2[k] >> 8) & 255, q2 = m2[k] & 255;
+            const bool v1 = q1 < s, v2 = q2 < s;
+            x[k][0] = a[p1 + p2 * lda];
+            x[k][1] = v2 ? a[p1 + q2 * lda] : T(0);
+            x[k][2] = v1 ? a[q1 + p2 * lda] : T(0);
+            x[k][3] = v1 && v2 ? a[q1 + q2 * lda] : T(0);
+            m1[k] |= i1 << 17, m2[k] |= i2 << 17;
+          } else if (e < total) {
+            const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
+            m1[k] = rpq[i];
+            if (j >= s || !(m1[k] & (1 << 16))) continue;
+            kind[k] = 3;
+            const int p = (m1[k] >> 8) & 255, q = m1[k] & 255;
+            x[k][0] = V[j + p * ldv], x[k][1] = V[j + q * ldv];
+            m1[k] |= i << 17, m2[k] = j;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (kind[k] == 0) continue;
+          if (kind[k] == 3) {
+            const int i = m1[k] >> 17, j = m2[k], p = (m1[k] >> 8) & 255, q = m1[k] & 255;
+            const T c = rot[2 * i], sn = rot[2 * i + 1];
+            V[j + p * ldv] = c * x[k][0] - sn * x[k][1];
+            V[j + q * ldv] = sn * x[k][0] + c * x[k][1];
+            continue;
+          }
+          const int i1 = m1[k] >> 17, i2 = m2[k] >> 17;
+          const int p1 = (m1[k] >> 8) & 255, q1 = m1[k] & 255, p2 = (m2[k] >> 8) & 255, q2 = m2[k] & 255;
+          const T c1 = rot[2 * i1], s1 = rot[2 * i1 + 1], c2 = rot[2 * i2], s2 = rot[2 * i2 + 1];
           const bool v1 = q1 < s, v2 = q2 < s;
-          const T x00 = a[p1 + p2 * lda], x01 = v2 ? a[p1 + q2 * lda] : T(0);
-          const T x10 = v1 ? a[q1 + p2 * lda] : T(0), x11 = v1 && v2 ? a[q1 + q2 * lda] : T(0);
           // rows (J_1^T), then columns (J_2)
-          const T r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
-          const T r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+          const T r00 = c1 * x[k][0] - s1 * x[k][2], r01 = c1 * x[k][1] - s1 * x[k][3];
+          const T r10 = s1 * x[k][0] + c1 * x[k][2], r11 = s1 * x[k][1] + c1 * x[k][3];
           T n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
           T n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
-          if (i1 == i2) {  // the pair's own block: its off-diagonal entry is annihilated
-            if (rot[4 * i1 + 1] != T(0)) n01 = n10 = T(0);
+          if (kind[k] == 2) {  // the pair's own block: its off-diagonal entry is annihilated
+            if (m1[k] & (1 << 16)) n01 = n10 = T(0);
             a[p1 + p1 * lda] = n00;
             if (v1) a[q1 + q1 * lda] = n11, a[p1 + q1 * lda] = n01, a[q1 + p1 * lda] = n10;
             continue;
@@ -150,14 +231,6 @@ __device__ int jacobi_sweeps(int s, T* a, int lda, T* V, int ldv, T* rot, double
           if (v2) a[p1 + q2 * lda] = n01, a[q2 + p1 * lda] = n01;
           if (v1) a[q1 + p2 * lda] = n10, a[p2 + q1 * lda] = n10;
           if (v1 && v2) a[q1 + q2 * lda] = n11, a[q2 + q1 * lda] = n11;
-        } else {
-          const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
-          if (j >= s || rot[4 * i + 1] == T(0)) continue;
-          const int pq = (int)rot[4 * i], p = pq >> 8, q = pq & 255;
-          const T c = rot[4 * i + 2], sn = rot[4 * i + 3];
-          const T vjp = V[j + p * ldv], vjq = V[j + q * ldv];
-          V[j + p * ldv] = c * vjp - sn * vjq;
-          V[j + q * ldv] = sn * vjp + c * vjq;
         }
       }
       __syncthreads();
@@ -181,6 +254,8 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
   const int nblk = half * (half + 1) / 2;
   unsigned short* blk = g_blk;
   fill_blocks(half, blk);
+  __shared__ int rpq[kMaxS / 2];
+  __shared__ float rcs[kMaxS];
   const int sh = s <= 32 ? 5 : (s <= 64 ? 6 : 7), sp = 1 << sh;
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     double o2 = 0.0;
@@ -194,7 +269,8 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
     const double off = sqrt(block_sum(o2, red));
     if (off <= rel_tol * fro || off == 0.0) return sweep;
     for (int r = 0; r < N - 1; ++r) {
-      // rot[4i .. 4i+3] = 256 p + q, c - 1 (0: identity), c, s; the diagonal is updated here
+      // rpq[i] = p << 8 | q (bit 16: the pair rotates); rot[3i ..] = c - 1, c, s in FP64 and
+      // rcs[2i ..] = c, s in FP32; the diagonal is updated here
       for (int i = threadIdx.x; i < half; i += blockDim.x) {
         int p, q;
         round_pair(N, r, i, p, q);
@@ -213,50 +289,81 @@ __device__ int jacobi_polish(int s, double* d, float* E, int lde, double* Dl, in
             rotate = true;
           }
         }
-        rot[4 * i + 0] = (double)(p * 256 + q) + (rotate ? 0.5 : 0.0);
-        rot[4 * i + 1] = cm1;
-        rot[4 * i + 2] = c;
-        rot[4 * i + 3] = sn;
+        rpq[i] = p << 8 | q | (rotate ? 1 << 16 : 0);
+        rot[3 * i + 0] = cm1;
+        rot[3 * i + 1] = c;
+        rot[3 * i + 2] = sn;
+        rcs[2 * i + 0] = (float)c;
+        rcs[2 * i + 1] = (float)sn;
       }
       __syncthreads();
-      for (int e = threadIdx.x; e < nblk + (half << sh); e += blockDim.x) {
-        if (e < nblk) {
-          const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
-          const double k1 = rot[4 * i1], k2 = rot[4 * i2];
-          const bool rot1 = k1 != floor(k1), rot2 = k2 != floor(k2);
-          if (!rot1 && !rot2) continue;
-          const int pq1 = (int)k1, p1 = pq1 >> 8, q1 = pq1 & 255;
-          if (i1 == i2) {  // the pair's own off-diagonal entry is annihilated (d done above)
+      // blocks of E between different pairs (the pair's own entry is annihilated; d was
+      // updated above), then columns p, q of Dl; loads of up to four items before stores
+      const int total = nblk + (half << sh);
+      for (int e0 = threadIdx.x; e0 < total; e0 += 4 * blockDim.x) {
+        int kind[4], m1[4], m2[4];
+        float x[4][4];
+        double y[4][2];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          const int e = e0 + k * blockDim.x;
+          kind[k] = 0;
+          if (e < nblk) {
+            const int i1 = blk[e] >> 8, i2 = blk[e] & 255;
+            m1[k] = rpq[i1], m2[k] = rpq[i2];
+            if (!((m1[k] | m2[k]) & (1 << 16))) continue;
+            const int p1 = (m1[k] >> 8) & 255, q1 = m1[k] & 255, p2 = (m2[k] >> 8) & 255, q2 = m2[k] & 255;
+            m1[k] |= i1 << 17, m2[k] |= i2 << 17;
+            if (i1 == i2) {
+              kind[k] = 2;
+              continue;
+            }
+            kind[k] = 1;
+            const bool v1 = q1 < s, v2 = q2 < s;
+            x[k][0] = E[p1 + p2 * lde];
+            x[k][1] = v2 ? E[p1 + q2 * lde] : 0.f;
+            x[k][2] = v1 ? E[q1 + p2 * lde] : 0.f;
+            x[k][3] = v1 && v2 ? E[q1 + q2 * lde] : 0.f;
+          } else if (e < total) {
+            const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
+            m1[k] = rpq[i];
+            if (j >= s || !(m1[k] & (1 << 16))) continue;
+            kind[k] = 3;
+            const int p = (m1[k] >> 8) & 255, q = m1[k] & 255;
+            y[k][0] = Dl[j + p * ldd], y[k][1] = Dl[j + q * ldd];
+            m1[k] |= i << 17, m2[k] = j;
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          if (kind[k] == 0) continue;
+          if (kind[k] == 3) {
+            // V' = V J with V = I + Dl
+            const int i = m1[k] >> 17, j = m2[k], p = (m1[k] >> 8) & 255, q = m1[k] & 255;
+            const double cm1 = rot[3 * i], cd = rot[3 * i + 1], sd = rot[3 * i + 2];
+            double np = cd * y[k][0] - sd * y[k][1], nq = sd * y[k][0] + cd * y[k][1];
+            if (j == p) np += cm1, nq += sd;
+            if (j == q) np -= sd, nq += cm1;
+            Dl[j + p * ldd] = np;
+            Dl[j + q * ldd] = nq;
+            continue;
+          }
+          const int p1 = (m1[k] >> 8) & 255, q1 = m1[k] & 255;
+          if (kind[k] == 2) {
             E[p1 + q1 * lde] = 0.f, E[q1 + p1 * lde] = 0.f;
             continue;
           }
-          const int pq2 = (int)k2, p2 = pq2 >> 8, q2 = pq2 & 255;
-          const float c1 = (float)rot[4 * i1 + 2], s1 = (float)rot[4 * i1 + 3];
-          const float c2 = (float)rot[4 * i2 + 2], s2 = (float)rot[4 * i2 + 3];
+          const int i1 = m1[k] >> 17, i2 = m2[k] >> 17, p2 = (m2[k] >> 8) & 255, q2 = m2[k] & 255;
+          const float c1 = rcs[2 * i1], s1 = rcs[2 * i1 + 1], c2 = rcs[2 * i2], s2 = rcs[2 * i2 + 1];
           const bool v1 = q1 < s, v2 = q2 < s;
-          const float x00 = E[p1 + p2 * lde], x01 = v2 ? E[p1 + q2 * lde] : 0.f;
-          const float x10 = v1 ? E[q1 + p2 * lde] : 0.f, x11 = v1 && v2 ? E[q1 + q2 * lde] : 0.f;
-          const float r00 = c1 * x00 - s1 * x10, r01 = c1 * x01 - s1 * x11;
-          const float r10 = s1 * x00 + c1 * x10, r11 = s1 * x01 + c1 * x11;
+          const float r00 = c1 * x[k][0] - s1 * x[k][2], r01 = c1 * x[k][1] - s1 * x[k][3];
+          const float r10 = s1 * x[k][0] + c1 * x[k][2], r11 = s1 * x[k][1] + c1 * x[k][3];
           const float n00 = c2 * r00 - s2 * r01, n01 = s2 * r00 + c2 * r01;
           const float n10 = c2 * r10 - s2 * r11, n11 = s2 * r10 + c2 * r11;
           E[p1 + p2 * lde] = n00, E[p2 + p1 * lde] = n00;
           if (v2) E[p1 + q2 * lde] = n01, E[q2 + p1 * lde] = n01;
           if (v1) E[q1 + p2 * lde] = n10, E[p2 + q1 * lde] = n10;
           if (v1 && v2) E[q1 + q2 * lde] = n11, E[q2 + q1 * lde] = n11;
-        } else {
-          // V' = V J with V = I + Dl
-          const int f = e - nblk, i = f >> sh, j = f & (sp - 1);
-          const double k = rot[4 * i];
-          if (j >= s || k == floor(k)) continue;
-          const int pq = (int)k, p = pq >> 8, q = pq & 255;
-          const double cd = rot[4 * i + 2], sd = rot[4 * i + 3], cm1 = rot[4 * i + 1];
-          const double djp = Dl[j + p * ldd], djq = Dl[j + q * ldd];
-          double np = cd * djp - sd * djq, nq = sd * djp + cd * djq;
-          if (j == p) np += cm1, nq += sd;
-          if (j == q) np -= sd, nq += cm1;
-          Dl[j + p * ldd] = np;
-          Dl[j + q * ldd] = nq;
         }
       }
       __syncthreads();
