@@ -318,8 +318,8 @@ def run_ours(args):
     if ul and ut > 0:
         if df:
             ops = uf / 2.0 * DF_OPS_PER_TERM
-            rooflines["update_fp64"] = {"kernel": "update_df_kernel (FP64 block updates in double-float on the FP32 "
-                                                  "pipes: X = V u_x, P = V u_p, W -= Y C, W <- W + W (T - I))",
+            rooflines["update_fp64"] = {"kernel": "update_df_async_kernel (FP64 block updates in double-float on "
+                                                  "the FP32 pipes: X = V u_x, P = V u_p, W -= Y C, W <- W + W (T - I))",
                                         "bound": "alu", "achieved": ops / ut / 1e12, "peak": fp32_peak / 2,
                                         "unit": "TFLOP/s", "frac": ops / ut / 1e12 / (fp32_peak / 2),
                                         "ops": "FP32 pipe operations, 15 per FP64-equivalent multiply-add",
@@ -510,8 +510,8 @@ def run_small_config(args):
         if nbytes64:
             # dense products: FP64 (n^2 * 8 B of A) in the FP64 phase, FP32 (n^2 * 4 B) in the FP32 one
             l64, l32 = i["spmm_launches_fp64"], i["spmm_launches"] - i["spmm_launches_fp64"]
-            t64 = i["phase_seconds_fp64"][0]
-            t32 = i["phase_seconds"][0] - t64
+            t64 = i["phase_seconds_fp64"]["spmm"]
+            t32 = i["phase_seconds"]["spmm"] - t64
             if l64:
                 row["dense_product_fp64_gbs"] = nbytes64 * l64 / t64 / 1e9
             if l32:
