@@ -967,32 +967,66 @@ __global__ void band_profile_kernel(int64_t n, const int64_t* __restrict__ rp, c
   if (threadIdx.x < nb) atomicAdd(&counts[threadIdx.x], sc[threadIdx.x]);
 }
 
-// RB rows per warp, PC columns per pass.
+// Y[:, c0 : c0 + pc] = A X[:, c0 : c0 + pc] for a dense symmetric A (column-major, lda):
+// column i of A is row i of A, so row i of Y is the dot product of A's column i (contiguous)
+// with X.  A CTA of 8 warps owns 8 RB consecutive columns (RB per warp); X's rows stream
+// through shared memory in slabs of kDenseSlab rows that all warps of the CTA share (row
+// stride padded so a quarter-warp's 16-byte reads hit distinct banks); lane l of a warp takes
+// slab rows l, l + 32, .. and reads A[c, i] coalesced across the warp, the four rows of a
+// slab unrolled so their loads are in flight together.  Partial sums are reduced across the
+// warp at the end in a fixed order.  A is read once per pass; X once per CTA.
+constexpr int kDenseSlab = 128;
 template <class T, int RB, int PC>
-__global__ void __launch_bounds__(256) spmm_dense_kernel(int64_t n, const T* __restrict__ A,
-                                                         int64_t lda, int p, int c0,
-                                                         const T* __restrict__ X, int ldx,
+__global__ void __launch_bounds__(256) spmm_dense_kernel(int64_t n, const T* __restrict__ A, int64_t lda, int p,
+                                                         int c0, const T* __restrict__ X, int ldx,
                                                          T* __restrict__ Y, int ldy) {
-  const int lane = threadIdx.x & 31;
-  const int64_t row0 = ((int64_t)blockIdx.x * (blockDim.x / kWarp) + threadIdx.x / kWarp) * RB;
-  if (row0 >= n) return;
+  // 16-byte reads at a row stride of 4 (mod 8) words (PC >= 16 bytes; narrower rows are read
+  // element by element)
+  constexpr int XS = sizeof(T) == 8 ? PC + 2 : PC + 4;
+  constexpr int VE = 16 / sizeof(T);                    // elements per 16-byte read
+  __shared__ __align__(16) T xs[kDenseSlab * XS];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t i0 = ((int64_t)blockIdx.x * 8 + warp) * RB;  // this warp's columns of A
   const int pc = min(PC, p - c0);
   T acc[RB][PC];
 #pragma unroll
   for (int r = 0; r < RB; ++r)
 #pragma unroll
     for (int j = 0; j < PC; ++j) acc[r][j] = T(0);
-  for (int64_t c = lane; c < n; c += kWarp) {
-    T x[PC];
-    const T* xr = X + c * ldx + c0;
+  for (int64_t cs = 0; cs < n; cs += kDenseSlab) {
+    __syncthreads();  // the previous slab is consumed
+    for (int e = threadIdx.x; e < kDenseSlab * PC; e += blockDim.x) {
+      const int cc = e / PC, j = e - cc * PC;
+      const int64_t c = cs + cc;
+      xs[cc * XS + j] = c < n && j < pc ? X[c * ldx + c0 + j] : T(0);
+    }
+    __syncthreads();
 #pragma unroll
-    for (int j = 0; j < PC; ++j) x[j] = j < pc ? xr[j] : T(0);
+    for (int u = 0; u < kDenseSlab / 32; ++u) {
+      const int cc = lane + 32 * u;
+      const int64_t c = cs + cc;
+      T a[RB];
 #pragma unroll
-    for (int r = 0; r < RB; ++r) {
-      const int64_t i = row0 + r;
-      const T a = i < n ? A[c + i * lda] : T(0);  // a_ci = a_ic (A symmetric)
+      for (int r = 0; r < RB; ++r) a[r] = c < n && i0 + r < n ? A[c + (i0 + r) * lda] : T(0);
+      T x[PC];
+      if constexpr (PC % VE != 0) {
 #pragma unroll
-      for (int j = 0; j < PC; ++j) acc[r][j] = fma(a, x[j], acc[r][j]);
+        for (int j = 0; j < PC; ++j) x[j] = xs[cc * XS + j];
+      }
+#pragma unroll
+      for (int v = 0; v < (PC % VE == 0 ? PC / VE : 0); ++v) {
+        if constexpr (sizeof(T) == 8) {
+          const double2 t = *reinterpret_cast<const double2*>(xs + cc * XS + VE * v);
+          x[VE * v] = t.x, x[VE * v + 1] = t.y;
+        } else {
+          const float4 t = *reinterpret_cast<const float4*>(xs + cc * XS + VE * v);
+          x[VE * v] = t.x, x[VE * v + 1] = t.y, x[VE * v + 2] = t.z, x[VE * v + 3] = t.w;
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+#pragma unroll
+        for (int j = 0; j < PC; ++j) acc[r][j] = fma(a[r], x[j], acc[r][j]);
     }
   }
 #pragma unroll
@@ -1002,7 +1036,7 @@ __global__ void __launch_bounds__(256) spmm_dense_kernel(int64_t n, const T* __r
   if (lane == 0) {
 #pragma unroll
     for (int r = 0; r < RB; ++r) {
-      const int64_t i = row0 + r;
+      const int64_t i = i0 + r;
       if (i < n)
 #pragma unroll
         for (int j = 0; j < PC; ++j)
@@ -1079,13 +1113,24 @@ template <class T>
 void launch_spmm_dense(int64_t n, const T* A, int64_t lda, int p, const T* X, int ldx, T* Y,
                        int ldy, cudaStream_t st) {
   if (n <= 0 || p <= 0) return;
-  constexpr int RB = 4, PC = 8;
+  // one pass over A for p <= 32 columns: RB x PC = 32 accumulators per thread
   const int threads = 256;
-  const int64_t blocks = ceil_div(ceil_div(n, RB), threads / kWarp);
-  for (int c0 = 0; c0 < p; c0 += PC) {
-    spmm_dense_kernel<T, RB, PC><<<(unsigned)blocks, threads, 0, st>>>(n, A, lda, p, c0, X, ldx, Y, ldy);
-    LB_LAUNCH_CHECK();
+  // columns past p cost FMAs (the FP64 product is bound by the FP64 FMA rate): the
+  // narrowest width that holds p
+  const unsigned g32 = (unsigned)ceil_div(n, 32);
+  if (p <= 2) {
+    spmm_dense_kernel<T, 4, 2><<<g32, threads, 0, st>>>(n, A, lda, p, 0, X, ldx, Y, ldy);
+  } else if (p <= 4) {
+    spmm_dense_kernel<T, 4, 4><<<g32, threads, 0, st>>>(n, A, lda, p, 0, X, ldx, Y, ldy);
+  } else if (p <= 8) {
+    spmm_dense_kernel<T, 4, 8><<<g32, threads, 0, st>>>(n, A, lda, p, 0, X, ldx, Y, ldy);
+  } else if (p <= 16) {
+    spmm_dense_kernel<T, 2, 16><<<(unsigned)ceil_div(n, 16), threads, 0, st>>>(n, A, lda, p, 0, X, ldx, Y, ldy);
+  } else {
+    for (int c0 = 0; c0 < p; c0 += 32)
+      spmm_dense_kernel<T, 1, 32><<<(unsigned)ceil_div(n, 8), threads, 0, st>>>(n, A, lda, p, c0, X, ldx, Y, ldy);
   }
+  LB_LAUNCH_CHECK();
 }
 
 template void launch_spmm_csr<double, double>(int64_t, const int64_t*, const int32_t*, const double*,

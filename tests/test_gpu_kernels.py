@@ -36,7 +36,7 @@ def test_spmm_csr_ci_band_matrix_ragged_tail():
     assert np.all(np.abs(Y - ref) <= 4 * np.finfo(float).eps * 80 * scale)
 
 
-@pytest.mark.parametrize("n,p", [(300, 4), (1031, 8), (2048, 13)])
+@pytest.mark.parametrize("n,p", [(1, 1), (300, 4), (1031, 8), (2048, 13), (8193, 21), (500, 32), (700, 9), (1500, 2), (999, 3)])
 def test_spmm_dense_matches_oracle(n, p):
     torch = cuda()
     import paper_2305_06668_gb300 as lb
