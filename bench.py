@@ -121,6 +121,14 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
+def mean_offdiag_row_norm(a):
+    """c = mean over rows of the off-diagonal row 2-norm (the learned preconditioner's
+    scale; the damped diagonal floors |d_i - theta| at it)."""
+    rows = np.repeat(np.arange(a.n), np.diff(a.row_ptr))
+    off = a.col_idx != rows
+    return float(np.mean(np.sqrt(np.bincount(rows[off], weights=a.val[off] ** 2, minlength=a.n))))
+
+
 def oracle_sample(a, x0):
     """Bounded sample of the oracle, as it stands, on the full workload: its initialisation
     alone, then the initialisation plus two iterations (about 10 s of CPU work)."""
@@ -254,8 +262,9 @@ def run_ours(args):
         return 0
     # the comparison the metric names: plain FP64 GPU solves of the same problem (median of
     # args.fp64_runs; the iteration count of FP64 LOBPCG on this matrix moves a lot with
-    # rounding), and the two ablations that split the gain into its precision and
-    # preconditioner parts: FP64 + learned, mixed + diagonal
+    # rounding), and the ablations that split the gain into its precision and
+    # preconditioner parts: FP64 + learned, mixed + diagonal, and mixed + damped diagonal
+    # (the classical control for the learned preconditioner)
     def timed_solve(**kw):
         s = lb.Solver(**t, extra=EXTRA, maxiter=args.maxiter, **kw)
         rr = s.solve(K, TOL, X0=x0)
@@ -265,8 +274,10 @@ def run_ours(args):
     r64 = sorted(plain, key=lambda rr: rr.info["seconds"])[len(plain) // 2]
     fp64_time = r64.info["seconds"]
     ablations = {}
+    c_rho = mean_offdiag_row_norm(a)  # the damped diagonal's floor: the learned model's own scale
     for name, kw in (("fp64_learned", dict(precision=lb.FP64, precond=lb.PREC_LEARNED, mlp_weights=weights)),
-                     ("mixed_diagonal", dict(precision=lb.MIXED))):
+                     ("mixed_diagonal", dict(precision=lb.MIXED)),
+                     ("mixed_damped_diagonal", dict(precision=lb.MIXED, precond_floor=c_rho))):
         rr = timed_solve(**kw)
         ablations[name] = {"seconds": rr.info["seconds"], "iterations": rr.info["iterations"],
                            "fp64_iterations": rr.info["fp64_iterations"], "status": lb.STATUS_NAMES[rr.status],
@@ -571,6 +582,40 @@ def run_gram_config(args):
     return 0
 
 
+def run_damping_config(args):
+    """Side line: the learned preconditioner against damped diagonal ones, a classical
+    control.  Held-out CI-like matrices (n = 100,000, seeds 2100-2102, not used in
+    training), k = 16 (+5 extra), tol 1e-8, FP64: the diagonal preconditioner with its
+    denominator floored at alpha * c for several alpha (c = mean off-diagonal row 2-norm, the
+    learned preconditioner's own scale), and the learned one."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_06668_gb300 as lb
+    import synth
+    w = lb.load_mlp_weights()
+    alphas = (0.0, 0.25, 1.0, 4.0, 16.0)
+    out = []
+    for seed in (2100, 2101, 2102):
+        a = synth.sparse_ci(n=100_000, seed=seed)
+        c = mean_offdiag_row_norm(a)
+        t = lb.upload_csr(a)
+        x0 = torch.from_numpy(synth.diag_guess(a.diag, K + EXTRA, seed=seed, noise=0.0)).cuda()
+        forms = [(f"diag_floor_{al:g}c", dict(precond_floor=al * c)) for al in alphas]
+        forms.append(("learned", dict(precond=lb.PREC_LEARNED, mlp_weights=w)))
+        for name, kw in forms:
+            s = lb.Solver(**t, extra=EXTRA, maxiter=20000, **kw)
+            r = s.solve(K, TOL, X0=x0)
+            s.close()
+            out.append({"seed": seed, "form": name, "c": c, "status": lb.STATUS_NAMES[r.status],
+                        "iterations": r.info["iterations"], "seconds": r.info["seconds"],
+                        "max_resnorm": float(np.max(r.resnorms)), "evals0": float(r.evals[0])})
+            log(json.dumps(out[-1]))
+    print(json.dumps({"side_line": "learned vs damped diagonal preconditioners (FP64, held-out seeds)",
+                      "n": 100000, "runs": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -579,10 +624,11 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense", "gram"],
+    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense", "gram", "damping"],
                     help="ci2m: the headline workload; batched: the 256-problem serving workload; "
                          "cfg1 / dense: the n=4096 sparse and n=8192 dense configurations (side lines); "
-                         "gram: the FP32 Gram kernels at n=2e6 (side line)")
+                         "gram: the FP32 Gram kernels at n=2e6; damping: learned vs damped diagonal "
+                         "preconditioners on held-out matrices (side lines)")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
@@ -598,6 +644,8 @@ def main():
         return run_small_config(args)
     if args.config == "gram":
         return run_gram_config(args)
+    if args.config == "damping":
+        return run_damping_config(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

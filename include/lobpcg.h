@@ -126,6 +126,11 @@ typedef struct {
   int tc_gram;                /* FP32 Gram matrices of the MIXED form: non-zero (default) on the
                                  tcgen05 tensor cores (lobpcg_gram_f32_tcgen05), 0 with warp-level
                                  mma.sync (lobpcg_gram_f32); both 3xTF32 */
+  double precond_floor;       /* diagonal preconditioner (not in the paper; a damped-diagonal
+                                 control for the learned one): the denominator d_i - theta_j is
+                                 replaced by sign(d_i - theta_j) max(|d_i - theta_j|, floor) with
+                                 this absolute floor (>= 0); 0 (default) = the guard of reading
+                                 R6 only.  The learned preconditioner ignores it */
 } lobpcg_options;
 
 typedef struct {

@@ -42,7 +42,7 @@ class _Options(C.Structure):
                 ("precision", C.c_int), ("tau_ortho", C.c_double), ("ortho_cap", C.c_int),
                 ("ortho2_cap", C.c_int), ("seed", C.c_uint64), ("mlp_weights", C.c_void_p), ("profile", C.c_int),
                 ("mixed_switch", C.c_double), ("autotune", C.c_int), ("ortho_trim", C.c_int),
-                ("df_products", C.c_int), ("tc_gram", C.c_int)]
+                ("df_products", C.c_int), ("tc_gram", C.c_int), ("precond_floor", C.c_double)]
 
 
 class _Info(C.Structure):
@@ -148,7 +148,8 @@ class Solver:
                  maxiter: int = 1000, tol_kind: int = 0, precond: int = PREC_DIAG, precision: int = FP64,
                  tau_ortho: float = 1e-14, ortho_cap: int = 6, ortho2_cap: int = 4, seed: int = 0,
                  mlp_weights=None, profile: bool = False, mixed_switch: float = 0.0, autotune: bool = False,
-                 ortho_trim: bool = True, df_products: int = 0, tc_gram: bool = True, mass=None, stream=None):
+                 ortho_trim: bool = True, df_products: int = 0, tc_gram: bool = True, precond_floor: float = 0.0,
+                 mass=None, stream=None):
         torch = _torch()
         L = lib()
         self._keep = [diag, row_ptr, col_idx, val, dense, mass]
@@ -177,6 +178,7 @@ class Solver:
         o.ortho_trim = 1 if ortho_trim else 0
         o.df_products = int(df_products)
         o.tc_gram = 1 if tc_gram else 0
+        o.precond_floor = float(precond_floor)
         w = None
         if mlp_weights is not None:
             w = np.ascontiguousarray(mlp_weights, dtype=np.float32)

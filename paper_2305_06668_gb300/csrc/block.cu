@@ -489,7 +489,7 @@ template <class T>
 __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __restrict__ AX, int ld,
                                const double* __restrict__ lam, int c0, int a,
                                const double* __restrict__ diag, int precond, T* __restrict__ W,
-                               int ldw, const double* __restrict__ diagB) {
+                               int ldw, const double* __restrict__ diagB, double floor) {
   // a 2-D walk (row, column) without 64-bit divisions: a warp covers 32 / a rows
   const int a_pad = a <= 1 ? 1 : (a <= 2 ? 2 : (a <= 4 ? 4 : (a <= 8 ? 8 : (a <= 16 ? 16 : 32))));
   const int rows_per_block = blockDim.x / a_pad;
@@ -497,7 +497,7 @@ __global__ void precond_kernel(int64_t n, const T* __restrict__ X, const T* __re
   const int rl = threadIdx.x / a_pad;
   if (j >= a) return;
   const double l = lam[c0 + j];
-  const T fl = (T)(1e-8 * fmax(1.0, fabs(l)));
+  const T fl = (T)fmax(1e-8 * fmax(1.0, fabs(l)), floor);  // reading R6, or the damping floor
   for (int64_t i = (int64_t)blockIdx.x * rows_per_block + rl; i < n; i += (int64_t)gridDim.x * rows_per_block) {
     const T r = AX[i * ld + c0 + j] - (T)l * X[i * ld + c0 + j];
     T w = r;
@@ -738,10 +738,11 @@ int launch_update_df(int64_t n, const UpdateJob<double>& job, const double* U, i
 
 template <class T>
 void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
-                    const double* diag, int precond, T* W, int ldw, cudaStream_t st, const double* diagB) {
+                    const double* diag, int precond, T* W, int ldw, cudaStream_t st, const double* diagB,
+                    double floor) {
   if (a <= 0 || n <= 0) return;
   precond_kernel<T><<<grid_for(n * a, 256), 256, 0, st>>>(n, X, AX, ld, lam, c0, a, diag, precond, W, ldw,
-                                                         diagB);
+                                                         diagB, floor);
   LB_LAUNCH_CHECK();
 }
 
@@ -780,8 +781,8 @@ template int gram_partials<double>(int64_t, const Cols<double>&, const Cols<doub
 template int gram_partials<float>(int64_t, const Cols<float>&, const Cols<float>&, bool, double*, int, cudaStream_t);
 template int launch_update<double>(int64_t, const UpdateJob<double>&, const double*, int, int, double, const double*, double*, int, cudaStream_t);
 template int launch_update<float>(int64_t, const UpdateJob<float>&, const double*, int, int, double, const double*, double*, int, cudaStream_t);
-template void launch_precond<double>(int64_t, const double*, const double*, int, const double*, int, int, const double*, int, double*, int, cudaStream_t, const double*);
-template void launch_precond<float>(int64_t, const float*, const float*, int, const double*, int, int, const double*, int, float*, int, cudaStream_t, const double*);
+template void launch_precond<double>(int64_t, const double*, const double*, int, const double*, int, int, const double*, int, double*, int, cudaStream_t, const double*, double);
+template void launch_precond<float>(int64_t, const float*, const float*, int, const double*, int, int, const double*, int, float*, int, cudaStream_t, const double*, double);
 template void launch_colmajor_to_rows<double, double>(int64_t, int, const double*, double*, int, cudaStream_t);
 template void launch_colmajor_to_rows<double, float>(int64_t, int, const double*, float*, int, cudaStream_t);
 template void launch_rows_to_colmajor<double, double>(int64_t, int, const double*, int, double*, cudaStream_t);

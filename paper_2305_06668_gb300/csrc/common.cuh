@@ -183,11 +183,12 @@ void launch_spmm_csr_df(int64_t n, const int64_t* rp, const int32_t* ci, const f
 
 // W~_ij = R_ij / guard(d_i - lam_{c0+j}) (precond 1) or R_ij (precond 0) with
 // R = AX[:, c0+j] - lam_{c0+j} X[:, c0+j], j < a.  With diagB (generalised problem: pass B X
-// as X) the denominator is d_i - lam diagB_i.
+// as X) the denominator is d_i - lam diagB_i.  `floor` > 0 floors |denominator| at it (sign
+// kept): the damped diagonal.
 template <class T>
 void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
                     const double* diag, int precond, T* W, int ldw, cudaStream_t st,
-                    const double* diagB = nullptr);
+                    const double* diagB = nullptr, double floor = 0.0);
 
 // row-major (ld) <-> column-major (n x p) conversions, optional precision change.
 template <class Tin, class Tout>

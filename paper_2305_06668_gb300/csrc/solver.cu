@@ -616,7 +616,7 @@ void precondition(lobpcg_ctx& c, const T* X, const T* AX, int ld, int m_conv, in
     mlp::launch_precond_learned<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, c.rho.as<float>(), c.cscale,
                                    c.colmax, c.mlp_params.as<float>(), W, ld, c.st);
   else
-    launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st);
+    launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st, nullptr, c.opt.precond_floor);
   c.prof.mark(PH_OTHER);
 }
 
@@ -962,7 +962,7 @@ PhaseOut run_lobpcg_gen(lobpcg_ctx& c, int k, int m, double tol, double tau, int
     return out;
   }
   int a = ls.m_act, m_conv = ls.m_conv, pw = 0;
-  launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag);
+  launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag, c.opt.precond_floor);
   int aw = gen_w_step(c, m, 0, a, tau, cap, cap2, cur);
   int it = 1;
   for (; it <= maxiter; ++it) {
@@ -997,7 +997,7 @@ PhaseOut run_lobpcg_gen(lobpcg_ctx& c, int k, int m, double tol, double tau, int
       update<double>(c, jq, c.up, s, pw_new, 1.0, nullptr, nullptr);         // B P, A P
     }
     cur = nxt, a = a_new, m_conv = ls.m_conv, pw = pw_new;
-    launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag);
+    launch_precond<double>(n, c.BX[cur], b.AX[cur], ld, c.lam, m_conv, a, c.A.diag, pc, b.W, ld, c.st, c.B.diag, c.opt.precond_floor);
     aw = gen_w_step(c, m, pw, a, tau, cap, cap2, cur);
   }
   out.iterations = std::min(it, maxiter);
@@ -1060,6 +1060,7 @@ extern "C" lobpcg_status lobpcg_options_default(lobpcg_options* opt) {
   opt->ortho_trim = 1;
   opt->df_products = 0;
   opt->tc_gram = 1;
+  opt->precond_floor = 0.0;
   return LOBPCG_OK;
 }
 
@@ -1087,6 +1088,8 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
     if (c->opt.ortho2_cap <= 0) c->opt.ortho2_cap = 4;
     require(c->opt.extra >= 0, "lobpcg_create: extra must be >= 0");
     require(c->opt.tol_kind == 0 || c->opt.tol_kind == 1, "lobpcg_create: tol_kind must be 0 or 1");
+    require(c->opt.precond_floor >= 0.0 && std::isfinite(c->opt.precond_floor),
+            "lobpcg_create: precond_floor must be finite and >= 0");
     require(c->opt.precond >= LOBPCG_PREC_NONE && c->opt.precond <= LOBPCG_PREC_LEARNED,
             "lobpcg_create: unknown preconditioner");
     require(c->opt.precision == LOBPCG_FP64 || c->opt.precision == LOBPCG_MIXED,

@@ -30,7 +30,7 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
     assert o.maxiter == 1000 and o.tau_ortho == 1e-14 and o.precond == lb.PREC_DIAG
     assert o.precision == lb.FP64 and o.ortho_cap == 6 and o.ortho2_cap == 4 and o.extra == 0
     assert o.autotune == 0 and o.mixed_switch == 0.0 and o.profile == 0 and o.ortho_trim == 1
-    assert o.df_products == 0 and o.tc_gram == 1
+    assert o.df_products == 0 and o.tc_gram == 1 and o.precond_floor == 0.0
     assert ctypes.sizeof(lb._Info) >= 8 * 6 * 2  # the info struct the binding reads
     assert L.lobpcg_options_default(None) == lb.EINVAL
     # NULL arguments are rejected before any device work

@@ -239,3 +239,36 @@ def test_ortho_trims_skip_only_passing_tests(precision):
     ref = oracle.lobpcg(a, a.diag, k + 1, x0, extra=1, tol=1e-8, maxiter=3000)
     assert ref.status == 0
     assert np.max(rel_eig_err(r1.evals, ref.evals[:k])) <= 1e-10
+
+
+def test_damped_diagonal_preconditioner_reaches_the_oracle_eigenpairs():
+    """precond_floor (the damped-diagonal control): 0 is the default path bit for bit; a
+    positive floor changes the iteration but not the limit, the oracle's eigenpairs
+    (eigenvalues to 1e-10; eigenvectors, reached by a different path, to the a-posteriori
+    bound sin(angle) <= ||r|| / gap of both runs plus 1e-7); a negative floor is an
+    argument error."""
+    torch = cuda()
+    import paper_2305_06668_gb300 as lb
+    a = synth.sparse_ci(n=60_001, seed=5)
+    k = 6
+    x0 = synth.diag_guess(a.diag, k, seed=5, noise=0.0)
+    ref = oracle.lobpcg(a, a.diag, k, x0, tol=1e-8)
+    base = _solve(torch, a, k, x0)
+    same = _solve(torch, a, k, x0, precond_floor=0.0)
+    assert np.array_equal(base.evals, same.evals) and base.info["iterations"] == same.info["iterations"]
+    rows = np.repeat(np.arange(a.n), np.diff(a.row_ptr))
+    off = a.col_idx != rows
+    c = float(np.mean(np.sqrt(np.bincount(rows[off], weights=a.val[off] ** 2, minlength=a.n))))
+    damped = _solve(torch, a, k, x0, precond_floor=c, maxiter=5000)
+    more = oracle.lobpcg(a, a.diag, k + 2, synth.diag_guess(a.diag, k + 2, seed=5, noise=0.0), tol=1e-9)
+    assert ref.status == 0 and damped.status == 0 and more.status == 0
+    assert np.max(rel_eig_err(damped.evals, ref.evals)) <= 1e-10
+    assert np.max(damped.resnorms) <= 1e-8
+    V = damped.evecs.cpu().numpy()
+    for j in range(k):
+        gap = min(abs(more.evals[j] - more.evals[i]) for i in range(k + 2) if i != j)
+        ang = float(cluster_angles(ref.evals[j:j + 1], ref.evecs[:, j:j + 1], V[:, j:j + 1])[0])
+        assert ang <= 1e-7 + (damped.resnorms[j] + ref.resnorms[j]) / gap, (j, ang, gap)
+    with pytest.raises(lb.LobpcgError) as e:
+        lb.Solver(**lb.upload_csr(a), precond_floor=-1.0)
+    assert e.value.status == lb.EINVAL
