@@ -100,10 +100,10 @@ typedef struct {
   int profile;                /* non-zero: fill lobpcg_info.phase_seconds (adds CUDA events) */
   double mixed_switch;        /* MIXED: leave FP32 once the k sought residuals are <= this;
                                  0 (default) = when the largest stops improving: once it is
-                                 below 1% of its first value, an iteration that cuts it by
-                                 less than 25% after three that cut it by a factor <= 0.6
-                                 each on geometric average, or no 10% drop in 2 iterations;
-                                 at any level, no 10% drop in 5 iterations */
+                                 below 1% of its first value, two iterations in a row that
+                                 cut it by less than 25% each after three that cut it by a
+                                 factor <= 0.6 each on geometric average, or no 10% drop in
+                                 2 iterations; at any level, no 10% drop in 5 iterations */
   int autotune;               /* non-zero: on the first solve with a given block width, time the
                                  CSR product kernel families on this matrix (a few products per
                                  precision, inside that solve) and keep the fastest.  Meant for

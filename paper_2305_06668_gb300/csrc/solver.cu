@@ -277,6 +277,7 @@ struct lobpcg_ctx {
   int* ictl = nullptr;  // [0..3] cholqr ctl, [4] sweeps, [5] finite flag
   LockState* lock = nullptr;
   DevBuf x0buf;        // column-major FP64 initial block when X0 == NULL
+  DevBuf xbest;        // the FP32 phase's X with the smallest largest-sought residual (reading R22)
   double* host = nullptr;  // pinned readback area
   Stats stats;
   Profiler prof;
@@ -626,6 +627,7 @@ struct PhaseOut {
   int m_conv = 0;
   bool converged = false;
   int xbuf = 0;  // which X buffer holds the result
+  const void* xbest = nullptr;  // stall exit of the mixed form: its best X (ld of the blocks)
   std::vector<double> lam, res;
 };
 
@@ -691,7 +693,8 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   int pw = 0;  // width of P in the current basis
   double best_rk = 1e300, first_rk = -1.0;
   int since_best = 0;
-  double rk_hist[4] = {0.0, 0.0, 0.0, 0.0};  // the last four largest sought residuals
+  double rk_hist[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // the last five largest sought residuals
+  double xbest_rk = 1e300;                         // largest sought residual of the best X
   int nhist = 0;
   double lbest = 1e300;
   int lsince = 0;
@@ -762,32 +765,45 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
       // mixed-precision switch: leave this precision once every one of the k sought
       // residuals is below switch_tol, or (switch_tol == 0) once the largest of them has
       // reached its rounding floor (reading R22): after it fell below 1% of its first
-      // value, either a sudden loss of a fast rate (over the three previous iterations it
-      // fell by a factor <= 0.6 per iteration on geometric average, this one cut it by
-      // less than 25%) or no 10% improvement for 2 iterations; at any level, no 10%
-      // improvement for 5 iterations
+      // value, either a sudden loss of a fast rate (over three iterations it fell by a
+      // factor <= 0.6 per iteration on geometric average, then two iterations in a row cut
+      // it by less than 25% each) or no 10% improvement for 2 iterations; at any level, no
+      // 10% improvement for 5 iterations
       double rk = 0.0;
       for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
       if (first_rk < 0.0) first_rk = rk;
-      bool rate_lost = false;
-      if (nhist >= 4 && rk <= 1e-2 * first_rk) {
-        const bool fast = rk_hist[3] <= 0.216 * rk_hist[0];  // (r3 / r0)^(1/3) <= 0.6
-        rate_lost = fast && rk > 0.75 * rk_hist[3];
+      if (rk < xbest_rk) {  // the FP64 phase starts from the best X, not from the last one
+        c.xbest.ensure((size_t)n * ld * sizeof(T));
+        LB_CUDA(cudaMemcpyAsync(c.xbest.p, b.X[nxt], (size_t)n * ld * sizeof(T), cudaMemcpyDeviceToDevice, c.st));
+        xbest_rk = rk;
       }
-      if (nhist < 4) rk_hist[nhist++] = rk;
-      else rk_hist[0] = rk_hist[1], rk_hist[1] = rk_hist[2], rk_hist[2] = rk_hist[3], rk_hist[3] = rk;
+      bool rate_lost = false;
+      if (nhist >= 5 && rk <= 1e-2 * first_rk) {
+        // rk_hist = r_{i-5} .. r_{i-1}, rk = r_i
+        const bool fast = rk_hist[3] <= 0.216 * rk_hist[0];  // (r_{i-2} / r_{i-5})^(1/3) <= 0.6
+        rate_lost = fast && rk_hist[4] > 0.75 * rk_hist[3] && rk > 0.75 * rk_hist[4];
+      }
+      if (nhist < 5) {
+        rk_hist[nhist++] = rk;
+      } else {
+        for (int h = 0; h < 4; ++h) rk_hist[h] = rk_hist[h + 1];
+        rk_hist[4] = rk;
+      }
       if (switch_tol > 0.0) {
         if (rk <= switch_tol) {
           cur = nxt;
+          out.xbest = c.xbest.p;
           break;
         }
       } else if (rate_lost) {
         cur = nxt;
+        out.xbest = c.xbest.p;
         break;
       } else if (rk < 0.9 * best_rk) {
         best_rk = rk, since_best = 0;
       } else if (++since_best >= 5 || (since_best >= 2 && best_rk <= 1e-2 * first_rk)) {
         cur = nxt;
+        out.xbest = c.xbest.p;
         break;
       }
     }
@@ -1252,7 +1268,8 @@ extern "C" lobpcg_status lobpcg_solve(lobpcg_ctx* c, int k, double tol, const do
       // continue in FP64 from the FP32 block
       Blocks<float>& b = c->b32;
       c->x0buf.ensure((size_t)n * m * sizeof(double));
-      launch_rows_to_colmajor<float, double>(n, m, b.X[p32.xbuf], b.ld, c->x0buf.as<double>(), c->st);
+      const float* x32 = p32.xbest ? static_cast<const float*>(p32.xbest) : b.X[p32.xbuf];
+      launch_rows_to_colmajor<float, double>(n, m, x32, b.ld, c->x0buf.as<double>(), c->st);
       launch_colmajor_to_rows<double, double>(n, m, c->x0buf.as<double>(), c->b64.X[0], c->b64.ld, c->st);
       c->df_on = c->opt.df_products >= 0;
       ph = run_lobpcg<double>(*c, k, m, tol, c->df_on ? std::max(tau, kTauDf) : tau,
@@ -1374,6 +1391,7 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   c->b32.buf.release();
   c->small.release();
   c->x0buf.release();
+  c->xbest.release();
   c->mlp_params.release();
   c->rho.release();
   if (c->host) cudaFreeHost(c->host);
@@ -1741,6 +1759,7 @@ extern "C" lobpcg_status lobpcg_solve_batched(lobpcg_ctx* const* ctxs, int nprob
       ctxs[i]->gbuf.release();
       ctxs[i]->b32.buf.release();
       ctxs[i]->x0buf.release();
+      ctxs[i]->xbest.release();
     }
   };
   std::vector<std::thread> pool;
