@@ -122,11 +122,21 @@ __global__ void __launch_bounds__(512) gram_kernel(int64_t n, Cols<T> A, Cols<T>
   }
 }
 
+// out[e] = sum over g in order of part[g][e].  The loads of eight partials are issued before
+// their adds (which stay in order), so the chain waits on memory once per eight.
 __global__ void reduce_kernel(const double* __restrict__ part, int nparts, int count,
                               double* __restrict__ out) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < count; e += gridDim.x * blockDim.x) {
     double s = 0.0;
-    for (int g = 0; g < nparts; ++g) s += part[(int64_t)g * count + e];
+    int g = 0;
+    for (; g + 8 <= nparts; g += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldg(part + (int64_t)(g + u) * count + e);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; g < nparts; ++g) s += part[(int64_t)g * count + e];
     out[e] = s;
   }
 }
