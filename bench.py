@@ -302,21 +302,35 @@ def run_ours(args):
         cols = c32 / l32
         # algorithmic bytes of one FP32 product: values + column indices + row pointers + read W + write AW
         b32 = nnz * (4 + 4) + (n + 1) * 8 + 2 * n * cols * 4
-        rooflines["spmm_fp32"] = {"kernel": "spmm_csr_window_kernel + spmm_csr_add_kernel (A W, FP32, band / "
+        rooflines["spmm_fp32"] = {"kernel": "spmm_band_packed_kernel + spmm_csr_add_kernel (A W, FP32, band / "
                                             "long-range split)", "bound": "hbm",
                                   "achieved": b32 / t32 / 1e9, "peak": hbm_peak, "unit": "GB/s",
                                   "frac": b32 / t32 / 1e9 / hbm_peak, "traffic": None,
                                   "bytes_per_launch": b32, "avg_launch_s": t32, "peak_source": peak_kind}
+    df = bool(infos[-1][1]["df_products"])
     if l64:
         t64 = ph64["spmm"] / l64
         cols = c64 / l64
         f64 = 2.0 * nnz * cols
-        rooflines["spmm_fp64"] = {"kernel": "spmm_csr_add_kernel<double> (A W, FP64 refinement, row-parallel)",
-                                  "bound": "alu",
-                                  "achieved": f64 / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
-                                  "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
-                                  "flops_per_launch": f64, "avg_launch_s": t64,
-                                  "peak_source": FP64_PEAK_SOURCE}
+        if df:
+            # double-float product on the FP32 pipes (the block's split into float pairs included)
+            ops = f64 / 2.0 * DF_OPS_PER_TERM
+            rooflines["spmm_fp64"] = {"kernel": "spmm_csr_df_kernel (A W, FP64 refinement in double-float on the "
+                                                "FP32 pipes, row-parallel)", "bound": "alu",
+                                      "achieved": ops / t64 / 1e12, "peak": fp32_peak / 2, "unit": "TFLOP/s",
+                                      "frac": ops / t64 / 1e12 / (fp32_peak / 2),
+                                      "ops": "FP32 pipe operations, 15 per FP64-equivalent multiply-add",
+                                      "fp64_equivalent_tflops": f64 / t64 / 1e12, "traffic": None,
+                                      "flops_per_launch": ops, "avg_launch_s": t64,
+                                      "peak_source": "FP32 FMA instruction rate measured in this run "
+                                                     "(lobpcg_probe_fma_rate / 2)"}
+        else:
+            rooflines["spmm_fp64"] = {"kernel": "spmm_csr_add_kernel<double> (A W, FP64 refinement, row-parallel)",
+                                      "bound": "alu",
+                                      "achieved": f64 / t64 / 1e12, "peak": fp64_peak, "unit": "TFLOP/s",
+                                      "frac": f64 / t64 / 1e12 / fp64_peak, "traffic": None,
+                                      "flops_per_launch": f64, "avg_launch_s": t64,
+                                      "peak_source": FP64_PEAK_SOURCE}
     # the FP64 block updates of the refinement, timed per launch with CUDA events.  With
     # double-float products (the default in the mixed form's refinement) they run on the FP32
     # pipes: each FP64-equivalent multiply-add is 15 FP32 operations (TwoProduct, TwoSum,
@@ -325,7 +339,6 @@ def run_ours(args):
     ut = sum(i["update_fp64_seconds"] for _, i, _, _ in infos)
     uf = sum(i["update_fp64_flops"] for _, i, _, _ in infos)
     ul = sum(i["update_fp64_launches"] for _, i, _, _ in infos)
-    df = bool(infos[-1][1]["df_products"])
     if ul and ut > 0:
         if df:
             ops = uf / 2.0 * DF_OPS_PER_TERM

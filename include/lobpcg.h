@@ -157,7 +157,8 @@ typedef struct {
   double update_fp64_flops;     /* their algorithmic flops, 2 n s q per product */
   int64_t update_fp64_launches; /* their number */
   int spmm_variant_fp32;        /* CSR product kernel in use: 0 default, 1 row-parallel,
-                                   2 vector gather, 3 band window with global gathers */
+                                   2 vector gather, 3 band window with global gathers,
+                                   4 band window on the unpacked band part (split FP32) */
   int spmm_variant_fp64;
   int w_dropped;                /* W columns dropped after an ortho(W~; Y) pass cap (reading R16) */
   int p_dropped;                /* P columns dropped: x_j did not move (R14) or after a pass cap (R16) */

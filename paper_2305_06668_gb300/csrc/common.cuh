@@ -91,7 +91,9 @@ __device__ __forceinline__ T warp_max(T v) {
 // variant: kSpmmAuto picks by precision, alignment and band; the others force one kernel
 // family (when the blocks allow it): the row-parallel kernel, the vector-gather kernel
 // (no band window), or the band window kernel with global gathers outside the band.
-enum { kSpmmAuto = 0, kSpmmRows = 1, kSpmmVec = 2, kSpmmBand = 3 };
+// kSpmmWindow applies to the band part of a split matrix: the window kernel on its unpacked
+// CSR arrays instead of the packed form (here it acts as kSpmmAuto).
+enum { kSpmmAuto = 0, kSpmmRows = 1, kSpmmVec = 2, kSpmmBand = 3, kSpmmWindow = 4 };
 template <class T, class V>
 void launch_spmm_csr(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const V* val,
                      int p, const T* X, int ldx, T* Y, int ldy, cudaStream_t st, int band = -1,
@@ -112,6 +114,15 @@ template <class V>
 void split_csr_scatter(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int band,
                        const int64_t* rp_band, int32_t* ci_band, V* v_band, const int64_t* rp_lr, int32_t* ci_lr,
                        V* v_lr, cudaStream_t st);
+// Packed form of the band part (FP32): entries as (col - row, value bits) pairs with the
+// column clamped into [row - band, row + band] and [0, n), rows padded to an even length
+// with a (0, 0.0f) entry; row pointers from the scan of split_even_counts.  launch_spmm_band_packed computes Y = A_band X from it and returns
+// false, without launching, when the blocks or the band do not fit its shared-memory window.
+void split_even_counts(int64_t n, const int32_t* cnt, int32_t* out, cudaStream_t st);
+void split_pack_band(int64_t n, int band, const int64_t* rp_band, const int32_t* ci_band, const float* v_band,
+                     const int64_t* rp_packed, int2* packed, cudaStream_t st);
+bool launch_spmm_band_packed(int64_t n, const int64_t* rp_packed, const int2* packed, int p, const float* X,
+                             int ldx, float* Y, int ldy, int band, cudaStream_t st);
 // Smallest half-width b in {16, ..., 2048} with 80% of the non-zeros at |col - row| <= b,
 // or -1 (synchronises the stream).
 int profile_band(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, int64_t nnz, cudaStream_t st);

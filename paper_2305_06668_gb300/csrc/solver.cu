@@ -194,58 +194,73 @@ struct Blocks {
 }  // namespace
 
 // FP32 copy of a CSR matrix split into A_band (|col - row| <= band) and A_lr (the rest),
-// both in CSR with the original row order of the entries.
+// both in CSR with the original row order of the entries, plus A_band in packed form
+// ((col - row, value) pairs, rows padded to even length) for the packed window kernel.
 struct SplitCSR {
-  DevBuf rp_buf, ci_buf, val_buf;
-  const int64_t *rp_band = nullptr, *rp_lr = nullptr;
+  DevBuf rp_buf, ci_buf, val_buf, rpk_buf, pk_buf;
+  const int64_t *rp_band = nullptr, *rp_lr = nullptr, *rp_pk = nullptr;
   const int32_t *ci_band = nullptr, *ci_lr = nullptr;
   const float *v_band = nullptr, *v_lr = nullptr;
-  int64_t nnz_band = 0, nnz_lr = 0;
+  const int2* pk = nullptr;
+  int64_t nnz_band = 0, nnz_lr = 0, nnz_pk = 0;
   int band = -1;
 
   void build(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val, int64_t nnz, int b,
              cudaStream_t st) {
     DevBuf cnt, scratch;
-    cnt.ensure((size_t)2 * std::max<int64_t>(n, 1) * sizeof(int32_t));
+    cnt.ensure((size_t)3 * std::max<int64_t>(n, 1) * sizeof(int32_t));
     scratch.ensure((size_t)split_scan_scratch(n) * sizeof(int64_t));
     int32_t* cb = cnt.as<int32_t>();
     int32_t* cl = cb + n;
+    int32_t* ce = cl + n;
     split_csr_count(n, row_ptr, col_idx, b, cb, cl, st);
+    split_even_counts(n, cb, ce, st);
     rp_buf.ensure((size_t)2 * (n + 1) * sizeof(int64_t));
+    rpk_buf.ensure((size_t)(n + 1) * sizeof(int64_t));
     int64_t* rpb = rp_buf.as<int64_t>();
     int64_t* rpl = rpb + (n + 1);
+    int64_t* rpk = rpk_buf.as<int64_t>();
     split_csr_rowptr(n, cb, rpb, scratch.as<int64_t>(), st);
     split_csr_rowptr(n, cl, rpl, scratch.as<int64_t>(), st);
-    int64_t tot[2] = {0, 0};
+    split_csr_rowptr(n, ce, rpk, scratch.as<int64_t>(), st);
+    int64_t tot[3] = {0, 0, 0};
     LB_CUDA(cudaMemcpyAsync(&tot[0], rpb + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LB_CUDA(cudaMemcpyAsync(&tot[1], rpl + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    LB_CUDA(cudaMemcpyAsync(&tot[2], rpk + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     LB_CUDA(cudaStreamSynchronize(st));
     if (tot[0] + tot[1] != nnz) throw std::runtime_error("band split: entry counts do not add up to nnz");
-    nnz_band = tot[0], nnz_lr = tot[1];
+    nnz_band = tot[0], nnz_lr = tot[1], nnz_pk = tot[2];
     const size_t nz = (size_t)std::max<int64_t>(nnz, 1);
     ci_buf.ensure(nz * sizeof(int32_t));
     val_buf.ensure(nz * sizeof(float));
+    pk_buf.ensure((size_t)std::max<int64_t>(nnz_pk, 2) * sizeof(int2));
     int32_t* cib = ci_buf.as<int32_t>();
     float* vb = val_buf.as<float>();
     split_csr_scatter<float>(n, row_ptr, col_idx, val, b, rpb, cib, vb, rpl, cib + tot[0], vb + tot[0], st);
+    split_pack_band(n, b, rpb, cib, vb, rpk, pk_buf.as<int2>(), st);
     LB_CUDA(cudaStreamSynchronize(st));
     cnt.release();
     scratch.release();
-    rp_band = rpb, rp_lr = rpl;
+    rp_band = rpb, rp_lr = rpl, rp_pk = rpk;
     ci_band = cib, ci_lr = cib + tot[0];
     v_band = vb, v_lr = vb + tot[0];
+    pk = pk_buf.as<int2>();
     band = b;
   }
-  // Y = A_band X, then Y += A_lr X
+  // Y = A_band X (the packed window kernel by default), then Y += A_lr X
   void apply(int64_t n, int p, const float* X, int ldx, float* Y, int ldy, cudaStream_t st,
              int variant = kSpmmAuto) const {
-    launch_spmm_csr<float, float>(n, rp_band, ci_band, v_band, p, X, ldx, Y, ldy, st, band, true, variant);
+    if (variant != kSpmmAuto || !launch_spmm_band_packed(n, rp_pk, pk, p, X, ldx, Y, ldy, band, st))
+      launch_spmm_csr<float, float>(n, rp_band, ci_band, v_band, p, X, ldx, Y, ldy, st, band, true,
+                                    variant == kSpmmWindow ? kSpmmAuto : variant);
     if (nnz_lr > 0) launch_spmm_csr_add<float, float>(n, rp_lr, ci_lr, v_lr, p, X, ldx, Y, ldy, st);
   }
   void release() {
     rp_buf.release();
     ci_buf.release();
     val_buf.release();
+    rpk_buf.release();
+    pk_buf.release();
   }
 };
 
@@ -388,9 +403,10 @@ void spmm_product(lobpcg_ctx& c, const T* X, int ldx, int p, T* Y, int ldy) {
 // Autotuner of the CSR product: on the first solve with block width p, time every kernel
 // family that applies to this matrix and precision (CUDA events, one warm-up and two timed
 // products each, on scratch blocks) and keep the fastest.  The default choice wins ties
-// within 2%.  Candidates: the default (window kernel on the band part of a split FP32
-// matrix, row-parallel for FP64, band window or vector gather otherwise), the row-parallel
-// kernel, the vector-gather kernel and the band window kernel with global gathers.
+// within 2%.  Candidates: the default (packed window kernel on the band part of a split
+// FP32 matrix, row-parallel for FP64, band window or vector gather otherwise), the window
+// kernel on the unpacked band part (split FP32 matrices), the row-parallel kernel, the
+// vector-gather kernel and the band window kernel with global gathers.
 template <class T>
 void autotune_spmm(lobpcg_ctx& c, int p, T* X, int ld, T* Y) {
   int& var = sizeof(T) == 4 ? c.var32 : c.var64;
@@ -398,7 +414,7 @@ void autotune_spmm(lobpcg_ctx& c, int p, T* X, int ld, T* Y) {
   if (c.A.fmt != LOBPCG_CSR || !c.opt.autotune || p <= 0 || tuned == p) return;
   std::vector<int> cand = {kSpmmAuto, kSpmmRows, kSpmmVec};
   if (c.band >= 0) cand.push_back(kSpmmBand);
-  if (sizeof(T) == 4 && c.split) cand = {kSpmmAuto, kSpmmRows, kSpmmBand};  // band part of the split
+  if (sizeof(T) == 4 && c.split) cand = {kSpmmAuto, kSpmmWindow, kSpmmRows, kSpmmBand};  // band part of the split
   cudaEvent_t e0, e1;
   LB_CUDA(cudaEventCreate(&e0));
   LB_CUDA(cudaEventCreate(&e1));

@@ -659,6 +659,182 @@ bool csr_window_launch(int64_t n, const int64_t* rp, const int32_t* ci, const V*
   return true;
 }
 
+__device__ __forceinline__ int4 lds_s32x4(unsigned addr) {
+  int4 r;
+  asm volatile("ld.shared.v4.s32 {%0, %1, %2, %3}, [%4];\n" : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w) : "r"(addr));
+  return r;
+}
+
+// Band part of a split matrix in packed form, FP32.  Each entry is one 8-byte pair
+// (col - row, value bits) with the column already inside [row - band, row + band] and
+// [0, n), and every row holds an even number of entries (a zero entry pads odd rows), so a
+// row starts on a 16-byte boundary and a lane reads two entries with one 16-byte load.  The
+// CTA owns rows [r0, r0 + R) and keeps rows [r0 - band, r0 + R + band) of X in shared
+// memory (row stride pp = p rounded up to 16 bytes).  Row pointers and entry pairs of
+// sub-blocks of RS rows are double-buffered in shared memory with 16-byte cp.async, one
+// sub-block ahead.  A group of L lanes takes two entries of a row per step and reads the
+// two gathered rows of X as L consecutive 16-byte vectors each.  Full batches of 2 G UNR
+// entries issue all their entry loads, then all their gathers; the rest of the row goes
+// in steps of 2 G entries, where pairs past the row's end read a zero pair (value 0, the
+// row's own X row), so no lane needs a predicate.  A transpose reduction sums the G groups.
+template <int L, int UNR, int RS>
+__global__ void __launch_bounds__(512, 1) spmm_band_packed_kernel(int64_t n, const int64_t* __restrict__ rpk,
+                                                               const int2* __restrict__ pk, int p,
+                                                               const float* __restrict__ X, int ldx,
+                                                               float* __restrict__ Y, int ldy, int R, int band,
+                                                               int pp, int cap) {
+  constexpr int VEC = 4;
+  constexpr int G = kWarp / L;
+  constexpr int BATCH = 2 * G * UNR;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int64_t r0 = (int64_t)blockIdx.x * R;
+  const int64_t r_end = min(n, r0 + R);
+  const int64_t lo = max((int64_t)0, r0 - band), hi = min(n, r_end + band);
+  const int win = (int)(hi - lo);
+  const int nvec = pp / VEC;
+  float* tile = reinterpret_cast<float*>(smem_raw);                                        // [win][pp]
+  int64_t* srp = reinterpret_cast<int64_t*>(smem_raw + (size_t)win * pp * sizeof(float));  // [2][RS + 1]
+  int2* spk = reinterpret_cast<int2*>(srp + 2 * (RS + 1));                                 // [2][cap] + zero pair
+  int2* zpair = spk + 2 * cap;
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x / kWarp, wpc = blockDim.x / kWarp;
+  for (int e = threadIdx.x; e < win * nvec; e += blockDim.x) {
+    const int rr = e / nvec, w = e - rr * nvec;
+    cp_async16_sp(tile + (int64_t)rr * pp + w * VEC, X + (lo + rr) * ldx + w * VEC);
+  }
+  if (threadIdx.x < 2) zpair[threadIdx.x] = make_int2(0, 0);
+  const unsigned row_bytes = (unsigned)(pp * sizeof(float));
+  const int nsub = (int)((r_end - r0 + RS - 1) / RS);
+  auto bounds = [&](int k, int64_t& eb, int64_t& ee) {
+    const int64_t a = r0 + (int64_t)k * RS, b = min(r_end, a + RS);
+    eb = rpk[a];
+    ee = rpk[b];
+  };
+  // row pointers and, when they fit, the entries of sub-block k (eb, ee even: 16-byte
+  // aligned source and size)
+  auto stage = [&](int k, int buf, int64_t eb, int64_t ee) {
+    const int64_t a = r0 + (int64_t)k * RS;
+    const int rows = (int)(min(r_end, a + RS) - a);
+    for (int i = threadIdx.x; i <= rows; i += blockDim.x) cp_async8_sp(srp + buf * (RS + 1) + i, rpk + a + i);
+    if (ee - eb <= cap) {
+      int2* d = spk + buf * cap;
+      for (int i = threadIdx.x; 2 * i < (int)(ee - eb); i += blockDim.x) cp_async16_sp(d + 2 * i, pk + eb + 2 * i);
+    }
+  };
+  int64_t eb, ee, nb = 0, ne = 0;
+  bounds(0, eb, ee);
+  stage(0, 0, eb, ee);
+  asm volatile("cp.async.commit_group;\n" ::);
+  if (nsub > 1) bounds(1, nb, ne);
+  const int g = lane / L, li = lane % L;
+  const bool has_vec = li < nvec;
+  const unsigned tile_s = (unsigned)__cvta_generic_to_shared(tile + li * VEC);
+  const unsigned zero_s = (unsigned)__cvta_generic_to_shared(zpair);
+  for (int k = 0; k < nsub; ++k) {
+    const int buf = k & 1;
+    if (k + 1 < nsub) stage(k + 1, buf ^ 1, nb, ne);  // buffer buf^1 was last read in k - 1
+    asm volatile("cp.async.commit_group;\n" ::);
+    int64_t fb = 0, fe = 0;
+    if (k + 2 < nsub) bounds(k + 2, fb, fe);  // in flight during this sub-block
+    asm volatile("cp.async.wait_group 1;\n" ::);
+    __syncthreads();
+    const bool staged = ee - eb <= cap;
+    const unsigned sp_s = (unsigned)__cvta_generic_to_shared(spk + buf * cap);
+    const int64_t* brp = srp + buf * (RS + 1);
+    const int64_t rb = r0 + (int64_t)k * RS;
+    const int rows = (int)(min(r_end, rb + RS) - rb);
+    for (int r = wid; r < rows; r += wpc) {
+      const int le0 = (int)(brp[r] - eb), le1 = (int)(brp[r + 1] - eb);
+      // this lane's vector of the row's own window row; an entry (d, v) gathers row + d
+      const unsigned rbase = tile_s + (unsigned)(rb + r - lo) * row_bytes;
+      float acc[VEC] = {0.f, 0.f, 0.f, 0.f};
+      int lj = le0;
+      if (staged) {
+        for (; lj + BATCH <= le1; lj += BATCH) {
+          int4 q[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) q[u] = lds_s32x4(sp_s + (unsigned)(lj + 2 * (u * G + g)) * 8u);
+          float4 xa[UNR], xb[UNR];
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            xa[u] = lds_f32x4(rbase + (unsigned)(q[u].x * (int)row_bytes));
+            xb[u] = lds_f32x4(rbase + (unsigned)(q[u].z * (int)row_bytes));
+          }
+#pragma unroll
+          for (int u = 0; u < UNR; ++u) {
+            vfma(__int_as_float(q[u].y), xa[u], acc);
+            vfma(__int_as_float(q[u].w), xb[u], acc);
+          }
+        }
+        for (; lj < le1; lj += 2 * G) {
+          const int e = lj + 2 * g;  // even: entries e and e + 1 are both in the row
+          const int4 q = lds_s32x4(e < le1 ? sp_s + (unsigned)e * 8u : zero_s);
+          const float4 xa = lds_f32x4(rbase + (unsigned)(q.x * (int)row_bytes));
+          const float4 xb = lds_f32x4(rbase + (unsigned)(q.z * (int)row_bytes));
+          vfma(__int_as_float(q.y), xa, acc);
+          vfma(__int_as_float(q.w), xb, acc);
+        }
+      } else {
+        for (; lj < le1; lj += 2 * G) {
+          const int e = lj + 2 * g;
+          const int4 q = e < le1 ? __ldg(reinterpret_cast<const int4*>(pk + eb + e)) : make_int4(0, 0, 0, 0);
+          const float4 xa = lds_f32x4(rbase + (unsigned)(q.x * (int)row_bytes));
+          const float4 xb = lds_f32x4(rbase + (unsigned)(q.z * (int)row_bytes));
+          vfma(__int_as_float(q.y), xa, acc);
+          vfma(__int_as_float(q.w), xb, acc);
+        }
+      }
+      bool owner;
+      const int off = reduce_scatter<L, VEC>(acc, lane, owner);
+      if (owner && has_vec) {
+        float* yr = Y + (rb + r) * ldy + li * VEC + off;
+#pragma unroll
+        for (int t = 0; t < Scatter<L, VEC>::keep; ++t)
+          if (li * VEC + off + t < p) yr[t] = acc[t];
+      }
+    }
+    eb = nb, ee = ne, nb = fb, ne = fe;
+    __syncthreads();  // buffer `buf` is refilled in the next iteration's prefetch
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::);
+}
+
+template <int L>
+bool band_packed_launch(int64_t n, const int64_t* rpk, const int2* pk, int p, const float* X, int ldx, float* Y,
+                        int ldy, int band, cudaStream_t st) {
+  constexpr int VEC = 4;
+  constexpr int RS = 32;
+  constexpr int UNR = 16 / (kWarp / L);  // 2 G UNR = 32 entries per step of the warp
+  const int pp = round_up(p, VEC);
+  if (ldx < pp || pp > L * VEC || band < 0) return false;
+  const size_t row_bytes = (size_t)pp * sizeof(float);
+  const int cap = 2048;  // entries per staged sub-block of RS rows (even)
+  const size_t fixed = (size_t)(2 * cap + 2) * sizeof(int2) + (size_t)2 * (RS + 1) * sizeof(int64_t);
+  const size_t budget = 216 * 1024;
+  if (budget <= fixed + row_bytes) return false;
+  // rows per CTA: as many as fit beside the two band halos, then evened out over whole
+  // waves of 152 CTAs
+  int64_t R = (int64_t)((budget - fixed) / row_bytes) - 2 * (int64_t)band;
+  R = R / RS * RS;
+  if (R < RS) return false;
+  const int64_t waves = ceil_div(ceil_div(n, R), 152);
+  R = std::min<int64_t>(R, ceil_div(ceil_div(n, 152 * waves), RS) * RS);
+  const int64_t win = std::min<int64_t>(n, R + 2 * (int64_t)band);
+  const size_t smem = (size_t)win * row_bytes + fixed;
+  if (smem > 220 * 1024) return false;
+  static const bool attr = [&] {
+    LB_CUDA(cudaFuncSetAttribute(spmm_band_packed_kernel<L, UNR, RS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 225 * 1024));
+    return true;
+  }();
+  (void)attr;
+  const int64_t ctas = ceil_div(n, R);
+  spmm_band_packed_kernel<L, UNR, RS><<<(unsigned)ctas, 512, smem, st>>>(n, rpk, pk, p, X, ldx, Y, ldy, (int)R,
+                                                                         band, pp, cap);
+  LB_LAUNCH_CHECK();
+  return true;
+}
+
 // Row-parallel product, Y += A X (ACC) or Y = A X.  Each group of L lanes owns one row of
 // Y (NV 16-byte vectors per lane, no cross-lane reduction) and walks that row's entries
 // UNR at a time, issuing all UNR gathers before using them; a warp thus keeps G = 32/L
@@ -950,6 +1126,32 @@ __global__ void split_scatter_kernel(int64_t n, const int64_t* __restrict__ rp, 
   }
 }
 
+// Row lengths of the packed band part: each count rounded up to even.
+__global__ void even_counts_kernel(int64_t n, const int32_t* __restrict__ cnt, int32_t* __restrict__ out) {
+  for (int64_t row = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; row < n; row += (int64_t)gridDim.x * blockDim.x)
+    out[row] = cnt[row] + (cnt[row] & 1);
+}
+
+// Packed band part: entry e of row i of A_band becomes (col - i, value bits) at rpk[i] + e;
+// an odd row gets a trailing (0, 0.0f) entry.  One warp per row (coalesced copies).
+__global__ void pack_band_kernel(int64_t n, int band, const int64_t* __restrict__ rpb,
+                                 const int32_t* __restrict__ cib, const float* __restrict__ vb,
+                                 const int64_t* __restrict__ rpk, int2* __restrict__ pk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * blockDim.x / kWarp;
+  for (int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / kWarp; row < n; row += nw) {
+    const int64_t b0 = rpb[row], b1 = rpb[row + 1], o = rpk[row];
+    // a column outside [0, n) (malformed input) is clamped so the product's gathers stay in
+    // its window; valid columns are unchanged
+    const int64_t cmin = max((int64_t)0, row - band), cmax = min(n - 1, row + band);
+    for (int64_t e = b0 + lane; e < b1; e += kWarp) {
+      const int64_t c = min(max((int64_t)cib[e], cmin), cmax);
+      pk[o + (e - b0)] = make_int2((int)(c - row), __float_as_int(vb[e]));
+    }
+    if (lane == 0 && ((b1 - b0) & 1)) pk[o + (b1 - b0)] = make_int2(0, 0);
+  }
+}
+
 // Fraction of non-zeros with |col - row| <= b for b in kBands (one pass over the rows).
 __global__ void band_profile_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
                                     unsigned long long* counts, int nb, const int* bands) {
@@ -1186,6 +1388,35 @@ void split_csr_scatter(int64_t n, const int64_t* rp, const int32_t* ci, const do
 }
 template void split_csr_scatter<float>(int64_t, const int64_t*, const int32_t*, const double*, int, const int64_t*,
                                        int32_t*, float*, const int64_t*, int32_t*, float*, cudaStream_t);
+
+void split_even_counts(int64_t n, const int32_t* cnt, int32_t* out, cudaStream_t st) {
+  if (n <= 0) return;
+  even_counts_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 256), 4864), 256, 0, st>>>(n, cnt, out);
+  LB_LAUNCH_CHECK();
+}
+
+void split_pack_band(int64_t n, int band, const int64_t* rpb, const int32_t* cib, const float* vb,
+                     const int64_t* rpk, int2* pk, cudaStream_t st) {
+  if (n <= 0) return;
+  pack_band_kernel<<<(unsigned)std::min<int64_t>(ceil_div(n, 8), 152 * 32), 256, 0, st>>>(n, band, rpb, cib, vb,
+                                                                                          rpk, pk);
+  LB_LAUNCH_CHECK();
+}
+
+bool launch_spmm_band_packed(int64_t n, const int64_t* rpk, const int2* pk, int p, const float* X, int ldx,
+                             float* Y, int ldy, int band, cudaStream_t st) {
+  if (n <= 0 || p <= 0) return true;
+  if (p > 32) throw std::invalid_argument("spmm: p > 32");
+  const bool vec_ok = (ldx % 4 == 0) && (ldy % 4 == 0) && ldx >= round_up(p, 4) &&
+                      !(reinterpret_cast<uintptr_t>(X) & 15) && !(reinterpret_cast<uintptr_t>(Y) & 15) &&
+                      !(reinterpret_cast<uintptr_t>(pk) & 15);
+  if (!vec_ok) return false;
+  // L lanes per gathered row, one 16-byte vector each: L = pow2 >= nvec
+  const int nvec = (p + 3) / 4;
+  if (nvec <= 2) return band_packed_launch<2>(n, rpk, pk, p, X, ldx, Y, ldy, band, st);
+  if (nvec <= 4) return band_packed_launch<4>(n, rpk, pk, p, X, ldx, Y, ldy, band, st);
+  return band_packed_launch<8>(n, rpk, pk, p, X, ldx, Y, ldy, band, st);
+}
 
 int profile_band(int64_t n, const int64_t* rp, const int32_t* ci, int64_t nnz, cudaStream_t st) {
   if (n <= 0 || nnz <= 0) return -1;
