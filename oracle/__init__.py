@@ -214,6 +214,41 @@ def precondition(R: np.ndarray, lam: np.ndarray, diag: np.ndarray, m_conv: int, 
     return W[:, :m_act]
 
 
+def tridiag_solve(dl: np.ndarray, d: np.ndarray, du: np.ndarray, shift: float, b: np.ndarray) -> np.ndarray:
+    """x = (T - shift I)^{-1} b for the tridiagonal T = (dl, d, du) (reading R24)."""
+    d = _f64(d)
+    n = d.shape[0]
+    dl = _f64(dl) if n > 1 else np.zeros(1)
+    du = _f64(du) if n > 1 else np.zeros(1)
+    b = _f64(b)
+    x = np.zeros(n)
+    lib().oracle_tridiag_solve(C.c_int64(n), _p(dl), _p(d), _p(du), C.c_double(shift), _p(b), _p(x))
+    return x
+
+
+def tridiag_of(A) -> tuple[np.ndarray, np.ndarray]:
+    """(dl, du): the first sub- and super-diagonals of A (CSR or dense)."""
+    op = _operator(A)
+    n = op.n
+    dl = np.zeros(max(n - 1, 1))
+    du = np.zeros(max(n - 1, 1))
+    lib().oracle_tridiag_of(C.byref(op.s), _p(dl), _p(du))
+    return dl[: max(n - 1, 0)], du[: max(n - 1, 0)]
+
+
+def precondition_tridiag(R: np.ndarray, lam: np.ndarray, dl: np.ndarray, diag: np.ndarray, du: np.ndarray,
+                         m_conv: int, m_act: int) -> np.ndarray:
+    """W[:, c] = (T - lam[m_conv + c] I)^{-1} R[:, m_conv + c] (reading R24)."""
+    R = np.asfortranarray(_f64(R))
+    n = R.shape[0]
+    W = np.zeros((n, m_act), order="F")
+    dl = _f64(dl) if n > 1 else np.zeros(1)
+    du = _f64(du) if n > 1 else np.zeros(1)
+    lib().oracle_precondition_tridiag(C.c_int64(n), C.c_int(m_conv), C.c_int(m_act), _p(R), _p(_f64(lam)),
+                                      _p(dl), _p(_f64(diag)), _p(du), _p(W))
+    return W
+
+
 def drop_unorthogonal_columns(W: np.ndarray, Y: np.ndarray | None, tau: float = 1e-14,
                               check_norm: bool = True) -> np.ndarray:
     """Reading R16: the columns of W kept (packed, in order)."""

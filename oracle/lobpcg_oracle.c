@@ -67,6 +67,13 @@
  *      than m_act columns).  A zero vector cannot be normalised by Algorithm 2, and in V it
  *      would produce a spurious Ritz value 0 with a zero "residual".  Columns that are
  *      merely small (rounding noise) are kept, as the printed algorithm does.
+ *  R24 Tridiagonal preconditioner (Sec. 4.4): w_j = (T - lambda_j I)^{-1} r_j with T the
+ *      diagonal and the first sub- and super-diagonals of A, solved by Gaussian
+ *      elimination with partial pivoting between neighbouring rows (the scheme of
+ *      LAPACK's tridiagonal solver).  A pivot smaller in magnitude than
+ *      1e-8 * max(1, |lambda_j|) is replaced by that value with its sign (sign(0) = +1),
+ *      the guard of R6.  With zero off-diagonals it is exactly the diagonal
+ *      preconditioner of R6.
  */
 #include "lobpcg_oracle.h"
 
@@ -559,6 +566,89 @@ void oracle_precondition(int64_t n, int m_conv, int m_act, const double* R, cons
   }
 }
 
+/* R24: x = (T - shift I)^{-1} b, T tridiagonal with sub-diagonal dl (T[i+1][i], n-1
+ * entries), diagonal d and super-diagonal du (T[i][i+1], n-1 entries).  Gaussian
+ * elimination with partial pivoting: at step i the pivot is the larger in magnitude of
+ * the two candidates in column i (rows i and i+1), and an interchange of the two rows
+ * puts a second super-diagonal entry (fill-in) into row i.  Then back substitution. */
+void oracle_tridiag_solve(int64_t n, const double* dl, const double* d, const double* du, double shift,
+                          const double* b, double* x) {
+  if (n <= 0) return;
+  const double fl = 1e-8 * fmax(1.0, fabs(shift));
+  double* p = malloc(sizeof(double) * (size_t)n);  /* pivots (diagonal of U) */
+  double* u1 = malloc(sizeof(double) * (size_t)n); /* first super-diagonal of U */
+  double* u2 = malloc(sizeof(double) * (size_t)n); /* second super-diagonal of U (fill-in) */
+  double* y = malloc(sizeof(double) * (size_t)n);  /* right-hand side, eliminated */
+  for (int64_t i = 0; i < n; ++i) {
+    p[i] = d[i] - shift;
+    u1[i] = i + 1 < n ? du[i] : 0.0;
+    u2[i] = 0.0;
+    y[i] = b[i];
+  }
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    /* rows i and i+1 hold column i: p[i] (row i) and dl[i] (row i+1) */
+    const double sub = dl[i];
+    if (fabs(p[i]) >= fabs(sub)) {
+      if (fabs(p[i]) < fl) p[i] = (p[i] >= 0.0 ? 1.0 : -1.0) * fl;
+      const double f = sub / p[i];
+      p[i + 1] -= f * u1[i];
+      y[i + 1] -= f * y[i];
+    } else {
+      /* interchange rows i and i+1: row i becomes (sub, p[i+1], u1[i+1]) */
+      const double piv = fabs(sub) < fl ? (sub >= 0.0 ? 1.0 : -1.0) * fl : sub;
+      const double f = p[i] / piv;
+      const double a1 = p[i + 1], a2 = u1[i + 1]; /* old row i+1: columns i+1, i+2 */
+      const double b1 = u1[i];                    /* old row i: column i+1 */
+      p[i] = piv;
+      u1[i] = a1;
+      u2[i] = a2;
+      p[i + 1] = b1 - f * a1;
+      u1[i + 1] = -f * a2;
+      const double yi = y[i];
+      y[i] = y[i + 1];
+      y[i + 1] = yi - f * y[i];
+    }
+  }
+  if (fabs(p[n - 1]) < fl) p[n - 1] = (p[n - 1] >= 0.0 ? 1.0 : -1.0) * fl;
+  for (int64_t i = n - 1; i >= 0; --i) {
+    double t = y[i];
+    if (i + 1 < n) t -= u1[i] * x[i + 1];
+    if (i + 2 < n) t -= u2[i] * x[i + 2];
+    x[i] = t / p[i];
+  }
+  free(p), free(u1), free(u2), free(y);
+}
+
+/* The first sub- and super-diagonals of A: dl[i] = A[i+1][i], du[i] = A[i][i+1]
+ * (duplicate CSR entries summed, as the product sums them). */
+void oracle_tridiag_of(const oracle_matrix* A, double* dl, double* du) {
+  const int64_t n = A->n;
+  for (int64_t i = 0; i + 1 < n; ++i) {
+    double lo = 0.0, up = 0.0;
+    if (A->dense) {
+      lo = A->dense[i * A->ld + (i + 1)]; /* column i, row i+1 (column-major) */
+      up = A->dense[(i + 1) * A->ld + i]; /* column i+1, row i */
+    } else {
+      for (int64_t e = A->row_ptr[i + 1]; e < A->row_ptr[i + 2]; ++e)
+        if (A->col_idx[e] == i) lo += A->val[e];
+      for (int64_t e = A->row_ptr[i]; e < A->row_ptr[i + 1]; ++e)
+        if (A->col_idx[e] == i + 1) up += A->val[e];
+    }
+    dl[i] = lo;
+    du[i] = up;
+  }
+}
+
+/* R24 on the active residual columns: W[:, c] = (T - lam_j I)^{-1} R[:, j], j = m_conv + c. */
+void oracle_precondition_tridiag(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+                                 const double* dl, const double* diag, const double* du, double* W) {
+#pragma omp parallel for schedule(static)
+  for (int c = 0; c < m_act; ++c) {
+    const int j = m_conv + c;
+    oracle_tridiag_solve(n, dl, diag, du, lam[j], R + (int64_t)j * n, W + (int64_t)c * n);
+  }
+}
+
 static void finish_outputs(const oracle_matrix* A, int64_t n, int k, const double* X,
                            const double* lam, double* evals, double* evecs, double* resnorms) {
   double* AXk = (double*)malloc(sizeof(double) * (size_t)n * k);
@@ -623,7 +713,8 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
   memset(&loc, 0, sizeof loc);
   if (k < 1 || opt->extra < 0 || 3 * (int64_t)m > n || !X0 || !evals || !evecs || !resnorms)
     return ORACLE_EINVAL;
-  if (opt->precond == 1 && !diag) return ORACLE_EINVAL;
+  if ((opt->precond == 1 || opt->precond == 3) && !diag) return ORACLE_EINVAL;
+  if (opt->precond < 0 || opt->precond > 3 || opt->precond == 2) return ORACLE_EINVAL;
   if (hist) hist->rows = 0;
 
   const int smax = 3 * m;
@@ -643,6 +734,12 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     return ORACLE_ENOMEM;
   }
   int status = ORACLE_ENOCONV;
+  double *tdl = NULL, *tdu = NULL; /* tridiagonal part of A (R24) */
+  if (opt->precond == 3) {
+    tdl = calloc((size_t)(n > 1 ? n - 1 : 1), sizeof(double));
+    tdu = calloc((size_t)(n > 1 ? n - 1 : 1), sizeof(double));
+    oracle_tridiag_of(A, tdl, tdu);
+  }
 
   /* ---- Algorithm 1, initialisation ---- */
   memcpy(X, X0, sizeof(double) * n * m);
@@ -667,7 +764,10 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     status = ORACLE_OK;
     goto done;
   }
-  oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);          /* W~ = T R */
+  if (opt->precond == 3)
+    oracle_precondition_tridiag(n, m_conv, m_act, R, lam, tdl, diag, tdu, W);   /* W~ = T R (R24) */
+  else
+    oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
   int w_cols = m_act; /* columns of W (R16) */
   {
     const int hits0 = loc.cap_hits;
@@ -739,7 +839,10 @@ int oracle_lobpcg(const oracle_matrix* A, const double* diag, const oracle_opts*
     block_times_small(n, s, V, p_cols, up, P);                            /* P = V u_p, AP = AV u_p */
     block_times_small(n, s, AV, p_cols, up, AP);
     have_p = p_cols;
-    oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);        /* W~ = T R */
+    if (opt->precond == 3)
+      oracle_precondition_tridiag(n, m_conv, m_act, R, lam, tdl, diag, tdu, W); /* W~ = T R (R24) */
+    else
+      oracle_precondition(n, m_conv, m_act, R, lam, diag, opt->precond, W);      /* W~ = T R */
     memcpy(Y, X, sizeof(double) * n * m);                                 /* Y = (X, P) */
     memcpy(Y + n * m, P, sizeof(double) * n * have_p);
     {
@@ -762,6 +865,7 @@ done:
   if (info) *info = loc;
   free(X), free(AX), free(W), free(AW), free(P), free(AP), free(R), free(Y), free(V);
   free(AV), free(a), free(U), free(lam_all), free(lam), free(up), free(nrm), free(conv);
+  free(tdl), free(tdu);
   return status;
 }
 

@@ -32,7 +32,7 @@ typedef struct {
   int extra;      /* block size m = k + extra (Sec. 2, larger block than sought) */
   int maxiter;    /* iteration cap of the main loop */
   int tol_kind;   /* 0: ||r_j||_2 <= tol;  1: rms(r_j) <= tol/10 and max|r_ij| <= tol */
-  int precond;    /* 0: none, 1: diagonal (diag(A) - theta)^-1 */
+  int precond;    /* 0: none, 1: diagonal (diag(A) - theta)^-1, 3: tridiagonal (R24) */
   int ortho_cap;  /* cap on Cholesky-QR passes in ortho(X)        (default 6) */
   int ortho2_cap; /* cap on projection passes in ortho(X, Y)      (default 4) */
   double tol;     /* residual tolerance */
@@ -125,6 +125,18 @@ int oracle_ortho_against(int64_t n, int p, double* X, int q, const double* Y, do
  * precond == 0 copies R.  R: n x m, W: n x m_act, column-major. */
 void oracle_precondition(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
                          const double* diag, int precond, double* W);
+
+/* Tridiagonal preconditioner (Sec. 4.4, reading R24).  oracle_tridiag_solve: x = (T -
+ * shift I)^{-1} b by Gaussian elimination with partial pivoting, T given by its
+ * sub-diagonal dl (T[i+1][i]), diagonal d and super-diagonal du (T[i][i+1]); pivots below
+ * 1e-8 max(1, |shift|) are replaced by that value with their sign.  oracle_tridiag_of: dl
+ * and du (n - 1 entries each) of A.  oracle_precondition_tridiag: W[:, c] = (T -
+ * lam[m_conv + c] I)^{-1} R[:, m_conv + c] (column-major, R n x m, W n x m_act). */
+void oracle_tridiag_solve(int64_t n, const double* dl, const double* d, const double* du, double shift,
+                          const double* b, double* x);
+void oracle_tridiag_of(const oracle_matrix* A, double* dl, double* du);
+void oracle_precondition_tridiag(int64_t n, int m_conv, int m_act, const double* R, const double* lam,
+                                 const double* dl, const double* diag, const double* du, double* W);
 
 /* Reading R16: drop the columns of W (n x p) whose largest |overlap| with Y (n x q) is
  * above sqrt(tau), and with check_norm those whose 2-norm differs from 1 by more than
