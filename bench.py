@@ -629,6 +629,54 @@ def run_damping_config(args):
     return 0
 
 
+def run_precond_config(args):
+    """Side line in the manner of the paper's Table 1 (Sec. 4.4): iterations and time of
+    LOBPCG with the diagonal, tridiagonal and learned preconditioners, FP64, tol 1e-8, on
+    cfg1 (n = 4096, k = 4), the dense CASSCF-like matrix (n = 8192, k = 8) and a held-out
+    CI-like matrix (n = 100,000, seed 2100, k = 16 + 5).  Each form: one warm-up solve, then
+    the best of `steps`; the preconditioner's own time per iteration from the profiled
+    phase timings."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2305_06668_gb300 as lb
+    import synth
+    w = lb.load_mlp_weights()
+    cases = []
+    a = synth.sparse_cfg1(n=4096, seed=0)
+    cases.append(("cfg1 n=4096 k=4", lb.upload_csr(a), synth.diag_guess(a.diag, 4, seed=0), 4, 0))
+    A, d = synth.dense_casscf(n=8192, seed=0, rank=256)
+    cases.append(("dense CASSCF-like n=8192 k=8", dict(diag=torch.from_numpy(d).cuda(), dense=torch.from_numpy(A).cuda()),
+                  synth.diag_guess(d, 8, seed=0), 8, 0))
+    c = synth.sparse_ci(n=100_000, seed=2100)
+    cases.append(("CI-like n=100000 seed 2100 k=16+5", lb.upload_csr(c),
+                  synth.diag_guess(c.diag, K + EXTRA, seed=2100, noise=0.0), K, EXTRA))
+    forms = (("diagonal", dict(precond=lb.PREC_DIAG)), ("tridiagonal", dict(precond=lb.PREC_TRIDIAG)),
+             ("learned", dict(precond=lb.PREC_LEARNED, mlp_weights=w)))
+    out = []
+    for name, mat, x0np, k, extra in cases:
+        x0 = torch.from_numpy(x0np).cuda()
+        for fname, kw in forms:
+            s = lb.Solver(**mat, extra=extra, maxiter=20000, profile=True, **kw)
+            s.solve(k, TOL, X0=x0)
+            best = None
+            for _ in range(max(1, args.steps)):
+                r = s.solve(k, TOL, X0=x0)
+                if best is None or r.info["seconds"] < best.info["seconds"]:
+                    best = r
+            s.close()
+            i = best.info
+            ph = i["phase_seconds"]
+            out.append({"case": name, "preconditioner": fname, "status": lb.STATUS_NAMES[best.status],
+                        "iterations": i["iterations"], "seconds": i["seconds"],
+                        "precond_ms_per_iteration": 1e3 * ph["precond"] / max(1, i["iterations"] + 1),
+                        "max_resnorm": float(np.max(best.resnorms)), "evals0": float(best.evals[0])})
+            log(json.dumps(out[-1]))
+    print(json.dumps({"side_line": "preconditioners as in Table 1: diagonal, tridiagonal, learned (FP64)",
+                      "runs": out}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -637,11 +685,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--maxiter", type=int, default=3000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
-    ap.add_argument("--config", default="ci2m", choices=["ci2m", "batched", "cfg1", "dense", "gram", "damping"],
+    ap.add_argument("--config", default="ci2m",
+                    choices=["ci2m", "batched", "cfg1", "dense", "gram", "damping", "precond"],
                     help="ci2m: the headline workload; batched: the 256-problem serving workload; "
                          "cfg1 / dense: the n=4096 sparse and n=8192 dense configurations (side lines); "
                          "gram: the FP32 Gram kernels at n=2e6; damping: learned vs damped diagonal "
-                         "preconditioners on held-out matrices (side lines)")
+                         "preconditioners on held-out matrices; precond: diagonal, tridiagonal and learned "
+                         "preconditioners as in the paper's Table 1 (side lines)")
     ap.add_argument("--nprob", type=int, default=256)
     ap.add_argument("--profile", action="store_true",
                     help="profiling run: time the mixed solves only (no FP64 comparison, e2e or CPU legs)")
@@ -659,6 +709,8 @@ def main():
         return run_gram_config(args)
     if args.config == "damping":
         return run_damping_config(args)
+    if args.config == "precond":
+        return run_precond_config(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

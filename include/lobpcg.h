@@ -64,7 +64,9 @@ typedef enum { LOBPCG_CSR = 0, LOBPCG_DENSE = 1 } lobpcg_format;
 typedef enum {
   LOBPCG_PREC_NONE = 0,   /* W~ = R */
   LOBPCG_PREC_DIAG = 1,   /* W~_ij = R_ij / (d_i - lambda_j)  (Sec. 2), guarded near zero */
-  LOBPCG_PREC_LEARNED = 2 /* diagonal preconditioner times a learned positive per-entry scale */
+  LOBPCG_PREC_LEARNED = 2, /* diagonal preconditioner times a learned positive per-entry scale */
+  LOBPCG_PREC_TRIDIAG = 3  /* W~_j = (T - lambda_j I)^{-1} R_j, T = the diagonal and first
+                              off-diagonals of A (Sec. 4.4), partial pivoting, guarded pivots */
 } lobpcg_precond;
 
 typedef enum {
@@ -266,6 +268,22 @@ LOBPCG_API lobpcg_status lobpcg_spmm_csr_f64_df(int64_t n, const int64_t* row_pt
 LOBPCG_API lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, const int32_t* col_idx,
                                   const double* val, int64_t nnz, int p, const float* X, int ldx,
                                   float* Y, int ldy, int band, int* band_used, lobpcg_stream stream);
+
+/* Tridiagonal preconditioner (Sec. 4.4; the option LOBPCG_PREC_TRIDIAG): W[:, j] =
+ * (T - shift[j] I)^{-1} R[:, j] for j < p, with T the tridiagonal matrix of sub-diagonal
+ * dl (dl[i] = T[i+1][i]), diagonal d and super-diagonal du (du[i] = T[i][i+1]); dl, du hold
+ * n - 1 entries (NULL allowed when n == 1).  R and W are row-major n x p with leading
+ * dimensions ldr, ldw >= p; all arrays are device memory owned by the caller.  The solve
+ * splits the rows into partitions of 1024, eliminates each with partial pivoting (row
+ * interchanges between neighbours), then couples the partitions through their first and
+ * last unknowns; pivots smaller than 1e-8 max(1, |shift[j]|) are replaced by that value
+ * with their sign.  It computes in FP32 (a preconditioner shapes a search direction; the
+ * solver orthonormalises the result in its own precision).  Allocates its scratch (about
+ * 24 n p bytes) on every call.  EINVAL for n < 1, p outside [1, 32], ld < p or a NULL
+ * array. */
+LOBPCG_API lobpcg_status lobpcg_precond_tridiag(int64_t n, const double* dl, const double* d, const double* du,
+                                                int p, const double* shift, const double* R, int ldr, double* W,
+                                                int ldw, lobpcg_stream stream);
 
 /* Y = A X for dense column-major symmetric A (lda >= n); X, Y as above, p <= 32. */
 LOBPCG_API lobpcg_status lobpcg_spmm_dense_f64(int64_t n, const double* A, int64_t lda, int p,

@@ -19,7 +19,7 @@ _lib = None
 
 OK, EINVAL, ENOMEM, ECUDA, ENOCONV, EBREAKDOWN = range(6)
 CSR, DENSE = 0, 1
-PREC_NONE, PREC_DIAG, PREC_LEARNED = 0, 1, 2
+PREC_NONE, PREC_DIAG, PREC_LEARNED, PREC_TRIDIAG = 0, 1, 2, 3
 FP64, MIXED = 0, 1
 PHASES = ("spmm", "rr_gram", "rr_eig", "update_lock", "precond", "ortho")
 STATUS_NAMES = {0: "OK", 1: "EINVAL", 2: "ENOMEM", 3: "ECUDA", 4: "ENOCONV", 5: "EBREAKDOWN"}
@@ -78,7 +78,7 @@ def lib():
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
                      "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32",
                      "lobpcg_probe_fma_rate", "lobpcg_gram_f64_df", "lobpcg_update_f64_df",
-                     "lobpcg_spmm_csr_f64_df", "lobpcg_gram_f32_tcgen05"):
+                     "lobpcg_spmm_csr_f64_df", "lobpcg_gram_f32_tcgen05", "lobpcg_precond_tridiag"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -269,6 +269,18 @@ def spmm_csr_f32(row_ptr, col_idx, val, X, band=-1, stream=None):
                                      C.c_int64(val.numel()), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), _ptr(Y),
                                      C.c_int(Y.stride(0)), C.c_int(band), C.byref(used), _stream(stream)))
     return Y, used.value
+
+
+def precond_tridiag(dl, d, du, shift, R, stream=None):
+    """W[:, j] = (T - shift[j] I)^{-1} R[:, j] for the tridiagonal T = (dl, d, du) (FP64 device
+    tensors; R row-major n x p).  Returns W (n x p, float64)."""
+    torch = _torch()
+    n, p = R.shape
+    W = torch.empty((n, p), dtype=torch.float64, device=R.device)
+    _check(lib().lobpcg_precond_tridiag(C.c_int64(n), _ptr(dl) if n > 1 else None, _ptr(d),
+                                        _ptr(du) if n > 1 else None, C.c_int(p), _ptr(shift), _ptr(R),
+                                        C.c_int(R.stride(0)), _ptr(W), C.c_int(W.stride(0)), _stream(stream)))
+    return W
 
 
 def spmm_dense(A, X, stream=None):

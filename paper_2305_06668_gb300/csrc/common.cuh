@@ -200,6 +200,18 @@ template <class T>
 void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
                     const double* diag, int precond, T* W, int ldw, cudaStream_t st,
                     const double* diagB = nullptr, double floor = 0.0);
+// Tridiagonal preconditioner (tridiag.cu): W[:, c] = (T - lam[c0 + c] I)^{-1} r_{c0+c} for
+// c < a, r = AX - X lam (or r = AX when X is NULL), T = (dl, d, du) in FP64; FP32 solve
+// through tridiag_scratch_floats(n, a) floats of scratch.  tridiag_extract fills dl
+// (A[i+1][i]) and du (A[i][i+1]) from CSR (duplicates summed) or dense column-major A.
+int64_t tridiag_partitions(int64_t n);
+size_t tridiag_scratch_floats(int64_t n, int a);
+void tridiag_extract(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,
+                     const double* dense, int64_t lda, double* dl, double* du, cudaStream_t st);
+template <class T>
+void launch_precond_tridiag(int64_t n, const T* X, const T* AX, int ld, const double* lam, int c0, int a,
+                            const double* d, const double* dl, const double* du, T* W, int ldw, float* scratch,
+                            cudaStream_t st);
 
 // row-major (ld) <-> column-major (n x p) conversions, optional precision change.
 template <class Tin, class Tout>

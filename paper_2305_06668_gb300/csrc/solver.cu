@@ -293,6 +293,8 @@ struct lobpcg_ctx {
   LockState* lock = nullptr;
   DevBuf x0buf;        // column-major FP64 initial block when X0 == NULL
   DevBuf xbest;        // the FP32 phase's X with the smallest largest-sought residual (reading R22)
+  DevBuf tri_offd;     // tridiagonal preconditioner: dl then du of A (n - 1 doubles each)
+  DevBuf tri_scratch;  // its FP32 scratch (tridiag_scratch_floats(n, a))
   double* host = nullptr;  // pinned readback area
   Stats stats;
   Profiler prof;
@@ -629,10 +631,16 @@ template <class T>
 void precondition(lobpcg_ctx& c, const T* X, const T* AX, int ld, int m_conv, int a, T* W) {
   const int pc = c.opt.precond == LOBPCG_PREC_NONE ? 0 : 1;
   c.prof.mark(PH_PRECOND);
-  if (c.use_learned)
+  if (c.use_learned) {
     mlp::launch_precond_learned<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, c.rho.as<float>(), c.cscale,
                                    c.colmax, c.mlp_params.as<float>(), W, ld, c.st);
-  else
+  } else if (c.opt.precond == LOBPCG_PREC_TRIDIAG) {
+    c.tri_scratch.ensure(tridiag_scratch_floats(c.A.n, a) * sizeof(float));
+    const int64_t no = std::max<int64_t>(c.A.n - 1, 1);
+    const double* dl = c.tri_offd.as<double>();
+    launch_precond_tridiag<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, dl, dl + no, W, ld,
+                              c.tri_scratch.as<float>(), c.st);
+  } else
     launch_precond<T>(c.A.n, X, AX, ld, c.lam, m_conv, a, c.A.diag, pc, W, ld, c.st, nullptr, c.opt.precond_floor);
   c.prof.mark(PH_OTHER);
 }
@@ -1122,7 +1130,7 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
     require(c->opt.tol_kind == 0 || c->opt.tol_kind == 1, "lobpcg_create: tol_kind must be 0 or 1");
     require(c->opt.precond_floor >= 0.0 && std::isfinite(c->opt.precond_floor),
             "lobpcg_create: precond_floor must be finite and >= 0");
-    require(c->opt.precond >= LOBPCG_PREC_NONE && c->opt.precond <= LOBPCG_PREC_LEARNED,
+    require(c->opt.precond >= LOBPCG_PREC_NONE && c->opt.precond <= LOBPCG_PREC_TRIDIAG,
             "lobpcg_create: unknown preconditioner");
     require(c->opt.precision == LOBPCG_FP64 || c->opt.precision == LOBPCG_MIXED,
             "lobpcg_create: unknown precision");
@@ -1176,6 +1184,14 @@ extern "C" lobpcg_status lobpcg_create(lobpcg_ctx** out, const lobpcg_matrix* A,
                                        c->scal, c->st);
       c->cscale = (float)(cs > 0 ? cs : 1.0);
     }
+    if (c->opt.precond == LOBPCG_PREC_TRIDIAG) {
+      const int64_t no = std::max<int64_t>(A->n - 1, 1);
+      c->tri_offd.ensure((size_t)2 * no * sizeof(double));
+      double* dl = c->tri_offd.as<double>();
+      LB_CUDA(cudaMemsetAsync(dl, 0, (size_t)2 * no * sizeof(double), c->st));
+      tridiag_extract(A->n, A->row_ptr, A->col_idx, A->val, A->fmt == LOBPCG_DENSE ? A->dense : nullptr, A->ld, dl,
+                      dl + no, c->st);
+    }
     c->opt.mlp_weights = nullptr;  // not retained
     c->sync();
     return LOBPCG_OK;
@@ -1191,7 +1207,8 @@ extern "C" lobpcg_status lobpcg_create_gen(lobpcg_ctx** out, const lobpcg_matrix
   lobpcg_options o;
   if (opt) o = *opt;
   else lobpcg_options_default(&o);
-  if (o.precision != LOBPCG_FP64 || o.precond == LOBPCG_PREC_LEARNED || o.df_products > 0)
+  if (o.precision != LOBPCG_FP64 || o.precond == LOBPCG_PREC_LEARNED || o.precond == LOBPCG_PREC_TRIDIAG ||
+      o.df_products > 0)
     return fail(nullptr, LOBPCG_EINVAL,
                 "lobpcg_create_gen: the generalised problem runs in FP64 with the diagonal or no preconditioner");
   lobpcg_ctx* c = nullptr;
@@ -1408,6 +1425,8 @@ extern "C" void lobpcg_destroy(lobpcg_ctx* c) {
   c->small.release();
   c->x0buf.release();
   c->xbest.release();
+  c->tri_offd.release();
+  c->tri_scratch.release();
   c->mlp_params.release();
   c->rho.release();
   if (c->host) cudaFreeHost(c->host);
@@ -1505,6 +1524,25 @@ extern "C" lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, 
       v32.release();
     }
     if (band_used) *band_used = b < 0 ? -1 : b;
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_precond_tridiag(int64_t n, const double* dl, const double* d, const double* du,
+                                                int p, const double* shift, const double* R, int ldr, double* W,
+                                                int ldw, lobpcg_stream stream) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(n >= 1 && d && shift && R && W && (n == 1 || (dl && du)), "lobpcg_precond_tridiag: NULL argument");
+    require(p >= 1 && p <= kMaxM && ldr >= p && ldw >= p, "lobpcg_precond_tridiag: need 1 <= p <= 32, ld >= p");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    DevBuf scratch, zero;
+    scratch.ensure(tridiag_scratch_floats(n, p) * sizeof(float));
+    if (n == 1) {  // no off-diagonals: any valid pointer will do, none is read
+      zero.ensure(sizeof(double));
+      dl = du = zero.as<double>();
+    }
+    launch_precond_tridiag<double>(n, nullptr, R, ldr, shift, 0, p, d, dl, du, W, ldw, scratch.as<float>(), st);
+    LB_CUDA(cudaStreamSynchronize(st));
     return LOBPCG_OK;
   });
 }
