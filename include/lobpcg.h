@@ -274,9 +274,9 @@ LOBPCG_API lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, 
  * dl (dl[i] = T[i+1][i]), diagonal d and super-diagonal du (du[i] = T[i][i+1]); dl, du hold
  * n - 1 entries (NULL allowed when n == 1).  R and W are row-major n x p with leading
  * dimensions ldr, ldw >= p; all arrays are device memory owned by the caller.  The solve
- * splits the rows into partitions of 1024, eliminates each with partial pivoting (row
- * interchanges between neighbours), then couples the partitions through their first and
- * last unknowns; pivots smaller than 1e-8 max(1, |shift[j]|) are replaced by that value
+ * splits the rows into partitions (32 to 1024 rows, chosen from n and p), eliminates each
+ * with partial pivoting (row interchanges between neighbours), then couples the partitions
+ * through their first and last unknowns; pivots smaller than 1e-8 max(1, |shift[j]|) are replaced by that value
  * with their sign.  It computes in FP32 (a preconditioner shapes a search direction; the
  * solver orthonormalises the result in its own precision).  Allocates its scratch (about
  * 24 n p bytes) on every call.  EINVAL for n < 1, p outside [1, 32], ld < p or a NULL

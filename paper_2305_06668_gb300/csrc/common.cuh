@@ -204,6 +204,7 @@ void launch_precond(int64_t n, const T* X, const T* AX, int ld, const double* la
 // c < a, r = AX - X lam (or r = AX when X is NULL), T = (dl, d, du) in FP64; FP32 solve
 // through tridiag_scratch_floats(n, a) floats of scratch.  tridiag_extract fills dl
 // (A[i+1][i]) and du (A[i][i+1]) from CSR (duplicates summed) or dense column-major A.
+int tridiag_partition_rows(int64_t n, int a);
 int64_t tridiag_partitions(int64_t n);
 size_t tridiag_scratch_floats(int64_t n, int a);
 void tridiag_extract(int64_t n, const int64_t* row_ptr, const int32_t* col_idx, const double* val,

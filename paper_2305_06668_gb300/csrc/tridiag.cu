@@ -1,8 +1,9 @@
 // Tridiagonal preconditioner (Sec. 4.4): W[:, c] = (T - lambda_{c0+c} I)^{-1} r_{c0+c}, with
 // T the diagonal and first off-diagonals of A and r = AX - X lambda formed on the fly.
 //
-// The n-row solve is split into partitions of kTriL rows (a SPIKE-type scheme, Polizzi and
-// Sameh, 2006).  With M = T - lambda I and M_p the block of partition p:
+// The n-row solve is split into partitions of L rows (a SPIKE-type scheme, Polizzi and
+// Sameh, 2006), L a power of two from 32 to 1024, the largest that still gives every SM
+// a few warps of (partition, column) threads.  With M = T - lambda I and M_p the block of partition p:
 //   1. per (partition, column): Gaussian elimination with partial pivoting of M_p (the
 //      scheme of LAPACK's tridiagonal solver, rows interchanged with their neighbour, a
 //      second super-diagonal as fill-in) for three right-hand sides: r_p, a_p e_1 and
@@ -23,7 +24,8 @@
 namespace lobpcg {
 namespace {
 
-constexpr int kTriL = 1024;  // rows per partition
+constexpr int kTriLMin = 32, kTriLMax = 1024;  // rows per partition
+constexpr int64_t kTriThreads = 152 * 128;     // (partition, column) threads wanted
 
 __device__ __forceinline__ float guard(float v, float fl) { return fabsf(v) < fl ? (v >= 0.f ? fl : -fl) : v; }
 
@@ -31,7 +33,7 @@ __device__ __forceinline__ float guard(float v, float fl) { return fabsf(v) < fl
 // during the elimination slots hold (pivot, u1, u2, rhs0, rhs1, rhs2), after the back
 // substitution slots 3..5 hold (y, v, w)
 template <class T>
-__global__ void __launch_bounds__(256) tri_partition_kernel(int64_t n, int64_t P, const T* __restrict__ X,
+__global__ void __launch_bounds__(256) tri_partition_kernel(int64_t n, int64_t P, int L, const T* __restrict__ X,
                                                             const T* __restrict__ AX, int ld,
                                                             const double* __restrict__ lam, int c0, int a,
                                                             const double* __restrict__ d,
@@ -42,7 +44,7 @@ __global__ void __launch_bounds__(256) tri_partition_kernel(int64_t n, int64_t P
   if (tid >= P * a) return;
   const int c = (int)(tid % a);
   const int64_t p = tid / a;
-  const int64_t s0 = p * kTriL, e0 = min(n, s0 + kTriL);
+  const int64_t s0 = p * L, e0 = min(n, s0 + L);
   const double th = lam[c0 + c];
   const float fl = (float)(1e-8 * fmax(1.0, fabs(th)));
   auto res = [&](int64_t i) -> float {
@@ -195,13 +197,13 @@ __global__ void __launch_bounds__(256) tri_reduced_kernel(int64_t P, int a, cons
 
 // x = y - u_{p-1} v - t_{p+1} w for every (row, column).
 template <class T>
-__global__ void tri_combine_kernel(int64_t n, int64_t P, int a, const float* __restrict__ S,
+__global__ void tri_combine_kernel(int64_t n, int64_t P, int L, int a, const float* __restrict__ S,
                                    const float* __restrict__ z, T* __restrict__ W, int ldw) {
   const int64_t total = n * a;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e / a;
     const int c = (int)(e - i * a);
-    const int64_t p = i / kTriL;
+    const int64_t p = i / L;
     const float* row = S + i * 6 * (int64_t)a + c;
     float x = row[3 * a];
     if (p > 0) x -= z[((p - 1) * a + c) * 2 + 0] * row[4 * a];
@@ -238,7 +240,15 @@ unsigned blocks_for(int64_t work, int threads) {
 
 }  // namespace
 
-int64_t tridiag_partitions(int64_t n) { return (n + kTriL - 1) / kTriL; }
+// Partition length for n rows and a columns: halved from kTriLMax while fewer than
+// kTriThreads (partition, column) pairs result, down to kTriLMin.
+int tridiag_partition_rows(int64_t n, int a) {
+  int L = kTriLMax;
+  while (L > kTriLMin && (n + L - 1) / L * a < kTriThreads) L /= 2;
+  return L;
+}
+
+int64_t tridiag_partitions(int64_t n) { return (n + kTriLMin - 1) / kTriLMin; }  // the most there can be
 
 size_t tridiag_scratch_floats(int64_t n, int a) {
   const int64_t P = tridiag_partitions(n);
@@ -260,20 +270,21 @@ void launch_precond_tridiag(int64_t n, const T* X, const T* AX, int ld, const do
                             const double* d, const double* dl, const double* du, T* W, int ldw, float* scratch,
                             cudaStream_t st) {
   if (n <= 0 || a <= 0) return;
-  const int64_t P = tridiag_partitions(n);
+  const int L = tridiag_partition_rows(n, a);
+  const int64_t P = (n + L - 1) / L;
   float* S = scratch;
   float* tips = S + (size_t)n * 6 * a;
   float* fwd = tips + (size_t)P * a * 6;
   float* z = fwd + (size_t)P * a * 3;
   const int64_t work = P * a;
-  tri_partition_kernel<T><<<(unsigned)((work + 127) / 128), 128, 0, st>>>(n, P, X, AX, ld, lam, c0, a, d, dl, du,
-                                                                        S, tips);
+  tri_partition_kernel<T><<<(unsigned)((work + 127) / 128), 128, 0, st>>>(n, P, L, X, AX, ld, lam, c0, a, d, dl,
+                                                                        du, S, tips);
   LB_LAUNCH_CHECK();
   if (P > 1) {
     tri_reduced_kernel<<<(unsigned)a, 256, 0, st>>>(P, a, tips, fwd, z);
     LB_LAUNCH_CHECK();
   }
-  tri_combine_kernel<T><<<blocks_for(n * a, 256), 256, 0, st>>>(n, P, a, S, z, W, ldw);
+  tri_combine_kernel<T><<<blocks_for(n * a, 256), 256, 0, st>>>(n, P, L, a, S, z, W, ldw);
   LB_LAUNCH_CHECK();
 }
 

@@ -1,7 +1,7 @@
 """The tridiagonal preconditioner (Sec. 4.4, reading R24) on the GPU against the oracle.
 
-The GPU solve is partitioned (1024-row blocks coupled through their end unknowns) and runs
-in FP32, so it is compared with the oracle's FP64 solve through the FP32 error bounds:
+The GPU solve is partitioned (blocks of 32 to 1024 rows, coupled through their end
+unknowns) and runs in FP32, so it is compared with the oracle's FP64 solve through the FP32 error bounds:
 a normwise backward error (residual) of 1e-5 and a forward error of 1e-5 times a bound on
 the condition number of T - shift I.  Inside LOBPCG a preconditioner only shapes the
 search direction: the solver's eigenvalues must meet |d lambda| <= 1e-10 max(1, |lambda|),
@@ -38,7 +38,8 @@ def _matvec(dl, d, du, s, x):
 @pytest.mark.parametrize("n,p", [(1, 1), (2, 3), (1023, 7), (1024, 21), (1025, 5), (4097, 21), (100_003, 8)])
 def test_diagonally_dominant_systems(n, p):
     """|d - shift| >= 2.5 > |dl| + |du|: kappa_inf <= (4.5 + 2) / (2.5 - 2) = 13.  Sizes span
-    one partition, its edges, a ragged tail and many partitions."""
+    one partition, ragged tails (down to a one-row last partition at n = 1025) and
+    thousands of partitions."""
     torch = cuda()
     g = np.random.default_rng(n + p)
     d = 3.0 + g.random(n)
@@ -55,8 +56,8 @@ def test_diagonally_dominant_systems(n, p):
 
 def test_indefinite_systems_with_row_interchanges():
     """Diagonal of random sign (|d| in [0.5, 1.5]), off-diagonals N(0, 0.6^2): the elimination
-    interchanges rows wherever |d - shift| < |dl|.  n = 3000 = three partitions, the last
-    one ragged.  Forward error against the oracle within 1e-5 kappa(T - shift I)."""
+    interchanges rows wherever |d - shift| < |dl|.  n = 3000: 94 partitions of 32 rows, the
+    last one ragged.  Forward error against the oracle within 1e-5 kappa(T - shift I)."""
     torch = cuda()
     g = np.random.default_rng(11)
     n, p = 3000, 5
@@ -78,8 +79,8 @@ def test_indefinite_systems_with_row_interchanges():
 
 
 def test_zero_diagonal_needs_interchanges_everywhere():
-    """T = tridiag(1, 0, 1), n = 4096 (four even partitions, each nonsingular): without
-    pivoting every first pivot is 0.  Integer data stay exact in FP32."""
+    """T = tridiag(1, 0, 1), n = 4096 (even partitions, each nonsingular): without pivoting
+    every first pivot is 0.  Integer data stay exact in FP32."""
     torch = cuda()
     n = 4096
     dl = du = np.ones(n - 1)
