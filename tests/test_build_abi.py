@@ -6,6 +6,7 @@ import subprocess
 import pytest
 
 import paper_2305_06668_gb300 as lb
+from tests.util import golden
 from paper_2305_06668_gb300 import build as gpu_build
 
 
@@ -27,7 +28,9 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
     L = lb.lib()
     o = lb._Options()
     assert L.lobpcg_options_default(ctypes.byref(o)) == lb.OK
-    assert o.maxiter == 1000 and o.tau_ortho == 1e-14 and o.precond == lb.PREC_DIAG
+    # the orthogonality threshold the paper uses in all its calculations (Sec. 4)
+    assert o.tau_ortho == golden()["tau_ortho"]["value"]
+    assert o.maxiter == 1000 and o.precond == lb.PREC_DIAG
     assert o.precision == lb.FP64 and o.ortho_cap == 6 and o.ortho2_cap == 4 and o.extra == 0
     assert o.autotune == 0 and o.mixed_switch == 0.0 and o.profile == 0 and o.ortho_trim == 1
     assert o.df_products == 0 and o.tc_gram == 1 and o.precond_floor == 0.0

@@ -8,7 +8,7 @@ import scipy.sparse.linalg as spla
 
 import oracle
 import synth
-from tests.util import cluster_angles, max_subspace_angle, rel_eig_err
+from tests.util import cluster_angles, golden, max_subspace_angle, rel_eig_err
 
 
 def test_diagonal_exact_start_exits_after_init():
@@ -113,11 +113,14 @@ def test_cfg1_invariants(cfg1_run):
 
 
 def test_cfg1_paper_statistics(cfg1_run):
-    """Sec. 3.2: at most 4 Cholesky-QR passes, ortho(X,Y) usually two passes."""
+    """Sec. 3.2: at most 4 Cholesky-QR passes, ortho(X,Y) usually one or two passes (the
+    printed values, tests/golden/paper_printed_values.json).  A claim about the paper's
+    matrices, so a miss on this recipe warns; the loops must not hit their caps."""
+    g = golden()
     _, r = cfg1_run
-    if r.info["cholqr_passes_max"] > 4:
+    if r.info["cholqr_passes_max"] > g["cholqr_passes_max"]["value"]:
         warnings.warn(f"Cholesky-QR passes {r.info['cholqr_passes_max']} > 4")
-    if r.info["ortho_passes_max"] > 3:
+    if r.info["ortho_passes_max"] > g["ortho_against_passes_typical"]["value"] + 1:
         warnings.warn(f"ortho(X,Y) passes {r.info['ortho_passes_max']} > 3")
     assert r.info["cap_hits"] == 0 and r.info["svqb"] == 0
 
@@ -145,14 +148,17 @@ def test_extra_block_columns():
 
 
 def test_tol_kind_rms_max():
+    """tol_kind 1 is the paper's Full-CI criterion (Sec. 4.1): RMS residual <= 1e-9 and largest
+    entry <= 1e-8 for tol = 1e-8 (values from tests/golden/paper_printed_values.json)."""
+    g = golden()["fci_convergence"]
     a = synth.sparse_cfg1(n=2000, seed=2)
-    r = oracle.lobpcg(a, a.diag, 2, synth.diag_guess(a.diag, 2, seed=1), tol=1e-8, tol_kind=1)
+    r = oracle.lobpcg(a, a.diag, 2, synth.diag_guess(a.diag, 2, seed=1), tol=g["max"], tol_kind=1)
     assert r.status == 0
     n = a.n
     R = oracle.apply(a, r.evecs) - r.evecs * r.evals
     # criterion holds (up to the drift between maintained and fresh AX)
-    assert np.all(np.linalg.norm(R, axis=0) / np.sqrt(n) <= 1e-9 * 1.5)
-    assert np.max(np.abs(R)) <= 1e-8 * 1.5
+    assert np.all(np.linalg.norm(R, axis=0) / np.sqrt(n) <= g["rms"] * 1.5)
+    assert np.max(np.abs(R)) <= g["max"] * 1.5
 
 
 def test_maxiter_reports_noconv_with_best_result():

@@ -42,3 +42,10 @@ def cluster_angles(lam_ref: np.ndarray, V_ref: np.ndarray, V: np.ndarray, rel: f
 
 def rel_eig_err(a: np.ndarray, b: np.ndarray) -> np.ndarray:
     return np.abs(a - b) / np.maximum(1.0, np.abs(b))
+
+
+def golden(name: str = "paper_printed_values.json") -> dict:
+    """A fixture of values printed in the paper (tests/golden/, each entry with its citation)."""
+    import json
+    import pathlib
+    return json.loads((pathlib.Path(__file__).resolve().parent / "golden" / name).read_text())
