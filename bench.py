@@ -47,6 +47,18 @@ def dist_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over the ranks of the default process group (x itself for one rank):
+    the bench's time is the slowest replica's."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_problem(n_rows=N_ROWS):
     import synth
     cache = f"/tmp/lobpcg_bench_ci_{n_rows}_{SEED}.npz"
@@ -244,11 +256,7 @@ def run_ours(args):
             infos.append((r.status, r.info, r.resnorms.max(), r.evals.copy()))
         ev1.record(stream)
         barrier()
-    total = ev0.elapsed_time(ev1) / 1e3
-    if world > 1:
-        tt = torch.tensor([total], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total = float(tt.item())
+    total = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, world)
     per_solve = total / args.steps
     statuses = [s for s, *_ in infos]
     last = infos[-1][1]
