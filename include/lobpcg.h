@@ -269,6 +269,17 @@ LOBPCG_API lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, 
                                   const double* val, int64_t nnz, int p, const float* X, int ldx,
                                   float* Y, int ldy, int band, int* band_used, lobpcg_stream stream);
 
+/* The rule by which the mixed form leaves FP32 (lobpcg_options.mixed_switch; with
+ * switch_tol = 0 the rounding-floor rule), replayed on the host over a history rk[0..n) of
+ * the largest sought residual norm per FP32 iteration: *leave_at receives the first i after
+ * which the solver leaves FP32, or -1.  switch_tol > 0: the first i with rk[i] <= switch_tol.
+ * switch_tol = 0: once rk[i] <= 1e-2 rk[0], the first i at which the residual fell by a
+ * factor <= 0.6 per iteration over iterations i-5 .. i-2 and then by less than 25% at both
+ * i-1 and i; or the first i at which the best rk so far has not improved by 10% for 2
+ * iterations (best <= 1e-2 rk[0]) or for 5 iterations.  No device work.  EINVAL for a NULL
+ * pointer (rk may be NULL when n == 0), n < 0 or switch_tol < 0. */
+LOBPCG_API lobpcg_status lobpcg_mixed_switch_replay(const double* rk, int n, double switch_tol, int* leave_at);
+
 /* Tridiagonal preconditioner (Sec. 4.4; the option LOBPCG_PREC_TRIDIAG): W[:, j] =
  * (T - shift[j] I)^{-1} R[:, j] for j < p, with T the tridiagonal matrix of sub-diagonal
  * dl (dl[i] = T[i+1][i]), diagonal d and super-diagonal du (du[i] = T[i][i+1]); dl, du hold

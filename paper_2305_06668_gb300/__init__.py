@@ -78,7 +78,8 @@ def lib():
                      "lobpcg_row_norms", "lobpcg_mlp_num_params", "lobpcg_solve_batched",
                      "lobpcg_spmm_csr_f32", "lobpcg_syev2_f64", "lobpcg_gram_f32", "lobpcg_update_f32",
                      "lobpcg_probe_fma_rate", "lobpcg_gram_f64_df", "lobpcg_update_f64_df",
-                     "lobpcg_spmm_csr_f64_df", "lobpcg_gram_f32_tcgen05", "lobpcg_precond_tridiag"):
+                     "lobpcg_spmm_csr_f64_df", "lobpcg_gram_f32_tcgen05", "lobpcg_precond_tridiag",
+                     "lobpcg_mixed_switch_replay"):
             getattr(L, name).restype = C.c_int
         L.lobpcg_last_error.restype = C.c_char_p
         L.lobpcg_last_error.argtypes = [C.c_void_p]
@@ -269,6 +270,17 @@ def spmm_csr_f32(row_ptr, col_idx, val, X, band=-1, stream=None):
                                      C.c_int64(val.numel()), C.c_int(p), _ptr(X), C.c_int(X.stride(0)), _ptr(Y),
                                      C.c_int(Y.stride(0)), C.c_int(band), C.byref(used), _stream(stream)))
     return Y, used.value
+
+
+def mixed_switch_replay(rk, switch_tol: float = 0.0) -> int:
+    """The FP32 iteration after which the mixed form would leave FP32 for the residual
+    history rk (largest sought residual per iteration), or -1 (lobpcg_mixed_switch_replay)."""
+    import numpy as np
+    r = np.ascontiguousarray(rk, dtype=np.float64)
+    out = C.c_int(0)
+    _check(lib().lobpcg_mixed_switch_replay(r.ctypes.data_as(C.c_void_p) if r.size else None, C.c_int(r.size),
+                                            C.c_double(switch_tol), C.byref(out)))
+    return out.value
 
 
 def precond_tridiag(dl, d, du, shift, R, stream=None):

@@ -22,6 +22,7 @@
 
 #include "../../include/lobpcg.h"
 #include "common.cuh"
+#include "switch_rule.cuh"
 #include "mlp.cuh"
 
 using namespace lobpcg;
@@ -715,11 +716,9 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
   ortho_against<T>(c, b.W, ld, a, cols1<T>(b.X[cur], ld, m), tau, cap, cap2, &aw);  // W = ortho(W~; X)
   apply_A<T>(c, b.W, ld, aw, b.AW, ld);                                 // AW = A W
   int pw = 0;  // width of P in the current basis
-  double best_rk = 1e300, first_rk = -1.0;
-  int since_best = 0;
-  double rk_hist[5] = {0.0, 0.0, 0.0, 0.0, 0.0};  // the last five largest sought residuals
+  MixedSwitch sw;                                  // when the mixed form leaves FP32
+  sw.switch_tol = switch_tol;
   double xbest_rk = 1e300;                         // largest sought residual of the best X
-  int nhist = 0;
   double lbest = 1e300;
   int lsince = 0;
 
@@ -786,46 +785,16 @@ PhaseOut run_lobpcg(lobpcg_ctx& c, int k, int m, double tol, double tau, int max
       break;
     }
     if (stall_exit) {
-      // mixed-precision switch: leave this precision once every one of the k sought
-      // residuals is below switch_tol, or (switch_tol == 0) once the largest of them has
-      // reached its rounding floor (reading R22): after it fell below 1% of its first
-      // value, either a sudden loss of a fast rate (over three iterations it fell by a
-      // factor <= 0.6 per iteration on geometric average, then two iterations in a row cut
-      // it by less than 25% each) or no 10% improvement for 2 iterations; at any level, no
-      // 10% improvement for 5 iterations
+      // mixed-precision switch (reading R22, switch_rule.cuh) on the largest of the k sought
+      // residuals; the FP64 phase starts from the best X, not from the last one
       double rk = 0.0;
       for (int j = 0; j < k; ++j) rk = std::max(rk, out.res[j]);
-      if (first_rk < 0.0) first_rk = rk;
-      if (rk < xbest_rk) {  // the FP64 phase starts from the best X, not from the last one
+      if (rk < xbest_rk) {
         c.xbest.ensure((size_t)n * ld * sizeof(T));
         LB_CUDA(cudaMemcpyAsync(c.xbest.p, b.X[nxt], (size_t)n * ld * sizeof(T), cudaMemcpyDeviceToDevice, c.st));
         xbest_rk = rk;
       }
-      bool rate_lost = false;
-      if (nhist >= 5 && rk <= 1e-2 * first_rk) {
-        // rk_hist = r_{i-5} .. r_{i-1}, rk = r_i
-        const bool fast = rk_hist[3] <= 0.216 * rk_hist[0];  // (r_{i-2} / r_{i-5})^(1/3) <= 0.6
-        rate_lost = fast && rk_hist[4] > 0.75 * rk_hist[3] && rk > 0.75 * rk_hist[4];
-      }
-      if (nhist < 5) {
-        rk_hist[nhist++] = rk;
-      } else {
-        for (int h = 0; h < 4; ++h) rk_hist[h] = rk_hist[h + 1];
-        rk_hist[4] = rk;
-      }
-      if (switch_tol > 0.0) {
-        if (rk <= switch_tol) {
-          cur = nxt;
-          out.xbest = c.xbest.p;
-          break;
-        }
-      } else if (rate_lost) {
-        cur = nxt;
-        out.xbest = c.xbest.p;
-        break;
-      } else if (rk < 0.9 * best_rk) {
-        best_rk = rk, since_best = 0;
-      } else if (++since_best >= 5 || (since_best >= 2 && best_rk <= 1e-2 * first_rk)) {
+      if (sw.step(rk)) {
         cur = nxt;
         out.xbest = c.xbest.p;
         break;
@@ -1524,6 +1493,22 @@ extern "C" lobpcg_status lobpcg_spmm_csr_f32(int64_t n, const int64_t* row_ptr, 
       v32.release();
     }
     if (band_used) *band_used = b < 0 ? -1 : b;
+    return LOBPCG_OK;
+  });
+}
+
+extern "C" lobpcg_status lobpcg_mixed_switch_replay(const double* rk, int n, double switch_tol, int* leave_at) {
+  return guarded(nullptr, [&]() -> lobpcg_status {
+    require(leave_at && n >= 0 && (rk || n == 0), "lobpcg_mixed_switch_replay: NULL argument or n < 0");
+    require(switch_tol >= 0.0, "lobpcg_mixed_switch_replay: switch_tol must be >= 0");
+    MixedSwitch sw;
+    sw.switch_tol = switch_tol;
+    *leave_at = -1;
+    for (int i = 0; i < n; ++i)
+      if (sw.step(rk[i])) {
+        *leave_at = i;
+        break;
+      }
     return LOBPCG_OK;
   });
 }
