@@ -57,6 +57,19 @@ def test_library_loads_and_reports_errors_without_gpu(libpath):
                                               None)
     assert upd(4, 4) == lb.EINVAL and upd(0, 4) == lb.EINVAL
     assert upd(1, 33) == lb.EINVAL and b"q <= 32" in L.lobpcg_last_error(None)
+    # tridiagonal preconditioner: NULL arrays, n < 1, p outside 1..32, ld < p
+    v = ctypes.c_void_p(16)  # never dereferenced: the checks come first
+    tri = lambda n, dl, p, ldr, ldw: L.lobpcg_precond_tridiag(ctypes.c_int64(n), dl, v, v, ctypes.c_int(p), v, v,
+                                                              ctypes.c_int(ldr), v, ctypes.c_int(ldw), None)
+    assert tri(10, None, 1, 1, 1) == lb.EINVAL and b"NULL" in L.lobpcg_last_error(None)
+    assert tri(0, v, 1, 1, 1) == lb.EINVAL
+    assert tri(10, v, 0, 1, 1) == lb.EINVAL and tri(10, v, 33, 33, 33) == lb.EINVAL
+    assert tri(10, v, 4, 3, 4) == lb.EINVAL and tri(10, v, 4, 4, 3) == lb.EINVAL
+    # switch-rule replay: NULL history with n > 0, n < 0
+    out = ctypes.c_int(7)
+    assert L.lobpcg_mixed_switch_replay(None, ctypes.c_int(3), ctypes.c_double(0.0), ctypes.byref(out)) == lb.EINVAL
+    assert L.lobpcg_mixed_switch_replay(None, ctypes.c_int(-1), ctypes.c_double(0.0), ctypes.byref(out)) == lb.EINVAL
+    assert L.lobpcg_mixed_switch_replay(None, ctypes.c_int(0), ctypes.c_double(0.0), None) == lb.EINVAL
 
 
 def test_no_cpu_fallback_in_product_package():
